@@ -1,0 +1,225 @@
+/*
+ * gamer_gb300.h -- C ABI of the GB300 (sm_103a) MUSCL-Hancock + Roe patch-group
+ * hydro step.
+ *
+ * The operation (paper Sec. 2, "Extension I: hydrodynamic solver"): advance
+ * each AMR patch group by one time step with the MUSCL-Hancock method and
+ * Roe's Riemann solver -- spatial data reconstruction, half-step prediction,
+ * Riemann solver, full-step update -- as an unsplit finite-volume scheme with a
+ * five-point stencil per direction.  A patch group is 16^3 cells; with the
+ * two-cell ghost shell that stencil needs its input is 20^3 cells.  The ghost
+ * data are prepared outside the solver (paper Sec. 2: "the operation of
+ * preparing the ghost-zone data"); gamer_fill_ghosts_uniform_* does that on
+ * the device for a uniform level.  Groups are independent within a step, so a
+ * batch of N groups of uneven AMR levels (each its own dt and dh) is one call.
+ *
+ * Conventions shared by every entry point:
+ *  - Array pointers are caller-owned DEVICE memory unless a function says
+ *    otherwise; the library never allocates, frees or synchronises on the
+ *    device path.  Work is enqueued on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream) and runs asynchronously.
+ *  - Layouts are C-contiguous, x fastest.  Conserved variables are ordered
+ *    (rho, rho*vx, rho*vy, rho*vz, E).
+ *  - Return codes: 0 success; negative GAMER_E* codes below.  Nothing is
+ *    launched when a call returns an error.  Per-group numerical events never
+ *    fail a call: they are reported in status[g] (GAMER_ST_* bits).
+ *  - N == 0 is a no-op returning 0.
+ *  - Device code never traps: bad data produce status bits, not faults.
+ */
+#ifndef GAMER_GB300_H
+#define GAMER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define GAMER_OK 0
+#define GAMER_E_NULL (-1)        /* a required pointer is NULL                        */
+#define GAMER_E_PARAM (-2)       /* bad size or parameter (N < 0, gamma <= 1, ...)      */
+#define GAMER_E_ALIGN (-3)       /* misaligned pointer                                  */
+#define GAMER_E_CUDA (-4)        /* CUDA launch / configuration error                  */
+#define GAMER_E_DEVICE (-5)      /* current device is not compute capability 10.x      */
+#define GAMER_E_OVERLAP (-6)     /* an output buffer overlaps an input buffer          */
+#define GAMER_E_WORKSPACE (-7)   /* workspace missing or too small                     */
+#define GAMER_E_TIMEOUT (-8)     /* a bounded host wait gave up (pipeline)             */
+
+/* ---- per-group status bits (status[g]) ---- */
+#define GAMER_ST_PREDICTOR_FALLBACK 0x1u /* a cell's half-step states were replaced (first order) */
+#define GAMER_ST_HLLE_FALLBACK      0x2u /* a face used HLLE instead of Roe                       */
+#define GAMER_ST_NONPOSITIVE_OUT    0x4u /* an updated cell has rho <= 0 or p <= 0 (or NaN)       */
+#define GAMER_ST_BAD_INPUT          0x8u /* non-finite read input, or dt < 0 / dh <= 0 / non-finite */
+#define GAMER_ST_INTERNAL_TIMEOUT  0x10u /* a bounded on-chip wait gave up; outputs are invalid  */
+
+/* ---- precision modes ---- */
+#define GAMER_MODE_F32 0   /* FP32 storage and arithmetic                                     */
+#define GAMER_MODE_MIXED 1 /* FP32 storage/arithmetic, pressure E - |m|^2/(2 rho) in FP64     */
+#define GAMER_MODE_F64 2   /* FP64 storage and arithmetic                                     */
+
+/* ---- scheme parameters ---- */
+typedef struct gh_params {
+    double gamma;               /* ratio of specific heats; finite and > 1                  */
+    double cfl;                 /* Courant number; used only by gamer_hydro_dt's callers    */
+    int32_t limiter;            /* slope limiter: 0 van Leer (default), 1 minmod, 2 MC      */
+    int32_t predictor_fallback; /* 0: cell average (default), 1: un-evolved face states   */
+    int32_t reserved[2];        /* must be 0                                                */
+} gh_params;
+
+/*
+ * gamer_hydro_advance_{f32,mixed,f64}: one MUSCL-Hancock + Roe step of N
+ * independent patch groups (paper Sec. 2: reconstruction, half-step
+ * prediction, Riemann solver, full-step update; unsplit; Roe's solver with
+ * Harten's entropy fix and an HLLE fallback for negative density or
+ * pressure).
+ *
+ *   in        [N][5][20][20][20] conserved state with the 2-cell ghost shell;
+ *             16-byte aligned.  The 8 corner 2x2x2 blocks and the depth-2
+ *             edge cells are never read.
+ *   out       [N][5][16][16][16] updated interior; element aligned; must not
+ *             overlap in.
+ *   face_flux [N][6][5][16][16] raw numerical flux F (not multiplied by dt)
+ *             through the six group faces, in the order -x, +x, -y, +y, -z, +z;
+ *             the two in-face indices are [k][j] for x faces, [k][i] for y
+ *             faces, [j][i] for z faces.  For the AMR coarse-fine flux fix-up.
+ *             May be NULL.
+ *   dt, dh    [N] time step and cell width of each group (FP64).
+ *   status    [N] GAMER_ST_* bits, or NULL.
+ *   partials  [N][6] FP64: { max over updated cells of max_d |v_d| + c,
+ *             sum rho, sum rho vx, sum rho vy, sum rho vz, sum E } of the
+ *             updated state, or NULL.  Input of gamer_hydro_dt.
+ *   N         number of groups (>= 0).
+ *   p         scheme parameters (host pointer).
+ *   stream    cudaStream_t.
+ * _f32 and _mixed take float arrays, _f64 double arrays.  In _mixed mode every
+ * recovery of the pressure from the conserved state (where E - rho v^2/2
+ * cancels in high-Mach cells) is done in FP64; everything else in FP32.
+ */
+int gamer_hydro_advance_f32(const float* in, float* out, float* face_flux, const double* dt,
+                            const double* dh, uint32_t* status, double* partials, int64_t N,
+                            const gh_params* p, void* stream);
+int gamer_hydro_advance_mixed(const float* in, float* out, float* face_flux, const double* dt,
+                              const double* dh, uint32_t* status, double* partials, int64_t N,
+                              const gh_params* p, void* stream);
+int gamer_hydro_advance_f64(const double* in, double* out, double* face_flux, const double* dt,
+                            const double* dh, uint32_t* status, double* partials, int64_t N,
+                            const gh_params* p, void* stream);
+
+/*
+ * gamer_fill_ghosts_uniform_{f32,f64}: ghost-zone preparation for a uniform
+ * level (paper Sec. 2: the ghost-zone data each patch needs before the solver
+ * runs).  level[G][5][16][16][16] holds the interiors of G = gx*gy*gz groups,
+ * group id (z*gy + y)*gx + x; writes in[G][5][20][20][20], every one of the
+ * 8000 cells (corners too) from the group itself or its neighbours.
+ * bc: 0 periodic, 1 zero-gradient (outflow: nearest interior cell of the
+ * level).  level and in must not overlap.  level element aligned, in
+ * 16-byte aligned (16-byte vector stores).
+ */
+int gamer_fill_ghosts_uniform_f32(const float* level, float* in, int32_t gx, int32_t gy,
+                                  int32_t gz, int32_t bc, void* stream);
+int gamer_fill_ghosts_uniform_f64(const double* level, double* in, int32_t gx, int32_t gy,
+                                  int32_t gz, int32_t bc, void* stream);
+
+/*
+ * gamer_hydro_dt: time step per AMR level and conservation totals, in FP64,
+ * from the per-group partials of gamer_hydro_advance_* (the CFL condition of
+ * the explicit scheme and the global sums the paper's code reduces over MPI):
+ *   dt_out[l]   = cfl * dh_level[l] / max_{g : level[g] == l} partials[g][0]
+ *                 (0 when no group of level l has a positive signal speed)
+ *   totals[5]   = sum over all groups of partials[g][1..5]      (may be NULL)
+ *   dt_group[g] = dt_out[level[g]], the next step's dt per group (may be NULL)
+ * level [N] int32 in [0, n_levels) or NULL (all groups in level 0);
+ * 1 <= n_levels <= 64; cfl finite and > 0.  dh_level [n_levels], dt_out
+ * [n_levels], totals [5], dt_group [N] are device arrays.  The reduction is
+ * deterministic (fixed order).  It needs device scratch memory of
+ * gamer_hydro_dt_workspace_bytes(N, n_levels) bytes, 8-byte aligned, owned by
+ * the caller (0 is returned for invalid sizes).
+ */
+size_t gamer_hydro_dt_workspace_bytes(int64_t N, int32_t n_levels);
+int gamer_hydro_dt(const double* partials, int64_t N, const int32_t* level, int32_t n_levels,
+                   const double* dh_level, double cfl, double* dt_out, double* totals,
+                   double* dt_group, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Device-resident uniform-level step as one CUDA graph (ghost fill -> hydro
+ * step -> dt reduction, no host round trip).
+ * gamer_level_graph_create captures, on a private stream, one step:
+ * level_a -> (ghost fill into tiles) -> hydro step -> level_b, followed by
+ * gamer_hydro_dt, whose dt_group output is the dt[] input of the next step.
+ * A run of steps alternates this graph with the one created with level_a and
+ * level_b swapped.  All pointers are caller-owned device arrays sized for
+ * G = gx*gy*gz groups: level_a, level_b [G][5][16]^3 and tiles [G][5][20]^3 of
+ * the mode's element type; face_flux [G][6][5][16][16] or NULL; dt_group,
+ * dh_group [G]; status [G] or NULL; partials [G][6]; dh_level, dt_level [1];
+ * totals [5] or NULL; workspace of gamer_hydro_dt_workspace_bytes(G, 1) bytes.
+ * dt_group must hold the first step's dt before the first launch.
+ * p->cfl is the Courant number of the dt reduction.  The buffers must outlive
+ * the graph.  gamer_level_graph_launch enqueues the step on `stream`.
+ */
+typedef struct gamer_level_graph gamer_level_graph;
+int gamer_level_graph_create(int32_t mode, void* level_a, void* level_b, void* tiles,
+                             void* face_flux, double* dt_group, const double* dh_group,
+                             uint32_t* status, double* partials, int32_t gx, int32_t gy,
+                             int32_t gz, int32_t bc, const gh_params* p, const double* dh_level,
+                             double* dt_level, double* totals, void* workspace,
+                             size_t workspace_bytes, gamer_level_graph** out);
+int gamer_level_graph_launch(gamer_level_graph* g, void* stream);
+int gamer_level_graph_destroy(gamer_level_graph* g);
+
+/*
+ * Streamed host pipeline (the paper overlaps CPU, GPU and disk work, Sec. 2
+ * and Sec. 3; here host->device copies, hydro steps and device->host copies
+ * of successive batches overlap on three streams).
+ * gamer_pipeline_create allocates three device buffer sets of batch_groups
+ * groups each for precision `mode` (with face-flux buffers if with_flux).
+ * gamer_pipeline_advance_host advances N groups held in HOST memory:
+ * in_host [N][5][20]^3, out_host [N][5][16]^3, face_flux_host [N][6][5][16][16]
+ * or NULL, dt_host, dh_host [N], status_host [N] or NULL, partials_host [N][6]
+ * or NULL -- the same layouts as gamer_hydro_advance_*, element type by mode.
+ * Host buffers should be page-locked (pinned) for the copies to overlap.  The
+ * call returns when all results are in host memory; it waits with a deadline
+ * (gamer_pipeline_set_timeout, default 60 s) and returns GAMER_E_TIMEOUT if
+ * the GPU has not finished by then.  It allocates nothing.  One pipeline must
+ * not be used by two host threads at once.
+ */
+typedef struct gamer_pipeline gamer_pipeline;
+int gamer_pipeline_create(int32_t mode, int64_t batch_groups, int32_t with_flux,
+                          gamer_pipeline** out);
+int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_host, void* out_host,
+                                void* face_flux_host, const double* dt_host,
+                                const double* dh_host, uint32_t* status_host,
+                                double* partials_host, int64_t N, const gh_params* p);
+int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds);
+int gamer_pipeline_destroy(gamer_pipeline* pl);
+
+/* Message for a GAMER_E* return code (static string). */
+const char* gamer_strerror(int code);
+
+/* 0 when the current CUDA device can run this library (compute capability
+ * 10.x, built for sm_103a), else GAMER_E_DEVICE or GAMER_E_CUDA. */
+int gamer_device_check(void);
+
+/* Library build identification (static string). */
+const char* gamer_version(void);
+
+/* Launch shape of gamer_hydro_advance_<mode> (mode = GAMER_MODE_*): CTAs per
+ * SM of the persistent grid, 0 = as many as fit (default).  Used by the
+ * autotuner; process-wide setting. */
+int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
+
+/* Throughput probes for the roofline denominators (not part of the scheme).
+ * kind 0: FP32 FMA, 1: FP64 FMA, 2: FP32 MUFU reciprocal -- a grid of
+ * 8 x 256 threads per SM, 8 dependent chains of `iters` operations per thread;
+ * buf: device scratch of >= 8 KB.  kind 3: copies n floats from buf to buf + n
+ * (buf holds 2n floats, 16-byte aligned, n a multiple of 4).  *work (host)
+ * receives the operation count (kinds 0-2) or bytes read + written (kind 3).
+ * The caller times the launch on `stream`. */
+int gamer_microbench(int32_t kind, int64_t iters, void* buf, int64_t n, double* work,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAMER_GB300_H */

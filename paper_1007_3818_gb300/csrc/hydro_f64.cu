@@ -1,0 +1,11 @@
+// hydro_f64.cu -- C-ABI entry point gamer_hydro_advance_f64 (one translation
+// unit per precision mode so the three instantiations compile in parallel).
+#include "hydro_launch.cuh"
+
+extern "C" int gamer_hydro_advance_f64(const double* in, double* out, double* face_flux,
+                                      const double* dt, const double* dh, uint32_t* status,
+                                      double* partials, int64_t N, const gh_params* p,
+                                      void* stream) {
+    return gamer::hydro_advance<GAMER_MODE_F64>(in, out, face_flux, dt, dh, status, partials, N, p,
+                                          stream);
+}

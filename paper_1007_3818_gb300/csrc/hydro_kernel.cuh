@@ -1,0 +1,684 @@
+// hydro_kernel.cuh -- the MUSCL-Hancock + Roe patch-group step for sm_103a.
+//
+// Paper Sec. 2: spatial data reconstruction, half-step prediction, Riemann
+// solver (Roe), full-step update; unsplit; five-point stencil per direction.
+// The scheme details follow the readings listed with the C ABI (primitive
+// reconstruction, van Leer / minmod / MC limiters, conservative Hancock
+// half-step with a cell-average fallback, Roe flux with Harten's smoothing of
+// |lambda| on the acoustic waves using Harten-Hyman widths from the Roe
+// intermediate states, HLLE with Einfeldt speeds as fallback).
+//
+// GB300 design (one CTA of 160 threads per patch group, persistent over the
+// batch, 2 CTAs per SM in FP32):
+//  * z-marching: the 20^3 input arrives one z-plane (5 x 20 x 20 values) at a
+//    time through the TMA engine (cp.async.bulk, 5 x 1600 B per plane in FP32)
+//    into a 3-slot shared ring, prefetched one iteration ahead, and is
+//    converted once per cell into a 3-plane ring of primitives.
+//  * per plane k: phase A predicts the 320 cells of the plane (16^2 interior +
+//    4 x 16 face-slab cells) -- two per thread; phase B solves the 800 Riemann
+//    problems whose fluxes touch the plane (272 x-faces, 272 y-faces from
+//    shared memory, 256 z-faces from registers) -- exactly five per thread;
+//    phase C finishes the update of plane k-1 and converts plane k+2.
+//  * each interior column (i,j) has an owner thread that keeps its z-face
+//    states, z-fluxes, the x/y flux divergence and the old state in registers,
+//    so nothing of the z direction goes through shared memory.
+//  * the epilogue reductions (max signal speed, conserved sums) are FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "gamer_gb300.h"
+
+namespace gamer {
+
+constexpr int kThreads = 160;
+constexpr int kPlane = 400;       // 20 x 20 cells per input plane
+constexpr int kFaceStride = 272;  // 16^2 interior + 16 slab entries per face array
+constexpr int kFluxStride = 544;  // 16 x 17 x-faces + 17 x 16 y-faces
+
+template <int MODE> struct Prec;
+template <> struct Prec<GAMER_MODE_F32> { using T = float; using P = float; };
+template <> struct Prec<GAMER_MODE_MIXED> { using T = float; using P = double; };
+template <> struct Prec<GAMER_MODE_F64> { using T = double; using P = double; };
+
+template <class T>
+struct alignas(16) Smem {
+    T raw[3][5 * kPlane];  // TMA ring of conserved input planes
+    T W[3][5 * kPlane];    // primitive planes
+    T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
+    T fxy[5 * kFluxStride];  // x- and y-face fluxes of the current plane
+    double red[kThreads / 32][6];
+    uint64_t mbar[3];
+    uint32_t status;
+    int32_t abort;
+};
+
+template <class T, class P>
+struct KConst {
+    T gamma, gm1;
+    P gm1p;
+    int limiter, pfb;
+};
+
+// ---------------------------------------------------------------------------
+// Pressure from a conserved state, given 1/rho in T.  MIXED recovers it in
+// FP64: 1/rho from the FP32 seed plus one Newton step, then E - |m|^2/(2 rho).
+template <int MODE, class T, class P>
+__device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KConst<T, P>& kc) {
+    if constexpr (MODE == GAMER_MODE_MIXED) {
+        const double rd = r;
+        double ird = ir;
+        ird = fma(ird, fma(-rd, ird, 1.0), ird);
+        const double a = m1, b = m2, c = m3;
+        const double ke = 0.5 * (a * a + b * b + c * c) * ird;
+        return static_cast<T>(kc.gm1p * (static_cast<double>(E) - ke));
+    } else {
+        return kc.gm1 * (E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
+    }
+}
+
+template <class T, class P>
+__device__ __forceinline__ T limit(T a, T b, const KConst<T, P>& kc) {
+    const T ab = a * b;
+    T r;
+    if (kc.limiter == 1) {
+        r = (a > T(0)) ? min_(a, b) : max_(a, b);
+    } else if (kc.limiter == 2) {
+        T m = min_(T(2) * abs_(a), T(2) * abs_(b));
+        m = min_(m, T(0.5) * abs_(a + b));
+        r = (a > T(0)) ? m : -m;
+    } else {
+        r = (T(2) * ab) * rcp_(a + b);
+    }
+    return (ab > T(0)) ? r : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// HLLE flux (rotated frame) with Einfeldt speed bounds.
+template <class T>
+__device__ __forceinline__ void hlle_rot(const T L[5], const T R[5], const T FL[5], const T FR[5],
+                                      T sl, T sr, T F[5]) {
+    const T bm = min_(sl, T(0));
+    const T bp = max_(sr, T(0));
+    const T inv = rcp_(bp - bm);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) F[i] = (bp * FL[i] - bm * FR[i] + bp * bm * (R[i] - L[i])) * inv;
+}
+
+// Roe flux through a face whose normal is the first velocity component of the
+// rotated states L, R = (rho, m_n, m_t1, m_t2, E).  Sets GAMER_ST_HLLE_FALLBACK
+// in st when the HLLE fallback is used.
+template <int MODE, class T, class P>
+__device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                        T F[5], uint32_t& st) {
+    const T irL = rcp_(L[0]), irR = rcp_(R[0]);
+    const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
+    const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
+    const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
+    const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
+    T FL[5], FR[5];
+    {
+        const T mL = L[0] * uL, mR = R[0] * uR;
+        FL[0] = mL;
+        FL[1] = mL * uL + pL;
+        FL[2] = mL * vL;
+        FL[3] = mL * wL;
+        FL[4] = (L[4] + pL) * uL;
+        FR[0] = mR;
+        FR[1] = mR * uR + pR;
+        FR[2] = mR * vR;
+        FR[3] = mR * wR;
+        FR[4] = (R[4] + pR) * uR;
+    }
+    const T cL = sqrt_(kc.gamma * pL * irL);
+    const T cR = sqrt_(kc.gamma * pR * irR);
+    const T HL = (L[4] + pL) * irL;
+    const T HR = (R[4] + pR) * irR;
+    const T rr = sqrt_(R[0] * irL);
+    const T i1 = rcp_(T(1) + rr);
+    const T uT = (uL + rr * uR) * i1;
+    const T vT = (vL + rr * vR) * i1;
+    const T wT = (wL + rr * wR) * i1;
+    const T HT = (HL + rr * HR) * i1;
+    const T q2 = uT * uT + vT * vT + wT * wT;
+    const T cT2 = kc.gm1 * (HT - T(0.5) * q2);
+    if (!(cT2 > T(0))) {
+        st |= GAMER_ST_HLLE_FALLBACK;
+        hlle_rot(L, R, FL, FR, uL - cL, uR + cR, F);
+        return;
+    }
+    const T cT = sqrt_(cT2);
+    const T rT = rr * L[0];
+    const T dr = R[0] - L[0], du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
+    const T ic2 = rcp_(cT2);
+    const T a1 = (dp - rT * cT * du) * (T(0.5) * ic2);
+    const T a2 = dr - dp * ic2;
+    const T a3 = rT * dv;
+    const T a4 = rT * dw;
+    const T a5 = (dp + rT * cT * du) * (T(0.5) * ic2);
+    const T K1u = uT - cT, K5u = uT + cT;
+    const T K1E = HT - uT * cT, K5E = HT + uT * cT;
+    // Roe intermediate states U*_L = U_L + a1 K1, U*_R = U_R - a5 K5
+    const T s1r = L[0] + a1, s1n = L[1] + a1 * K1u, s1a = L[2] + a1 * vT, s1b = L[3] + a1 * wT,
+            s1E = L[4] + a1 * K1E;
+    const T s4r = R[0] - a5, s4n = R[1] - a5 * K5u, s4a = R[2] - a5 * vT, s4b = R[3] - a5 * wT,
+            s4E = R[4] - a5 * K5E;
+    const T is1 = rcp_(s1r), is4 = rcp_(s4r);
+    const T p1 = pressure<MODE>(s1r, s1n, s1a, s1b, s1E, is1, kc);
+    const T p4 = pressure<MODE>(s4r, s4n, s4a, s4b, s4E, is4, kc);
+    if (!(s1r > T(0) && p1 > T(0) && s4r > T(0) && p4 > T(0))) {
+        st |= GAMER_ST_HLLE_FALLBACK;
+        hlle_rot(L, R, FL, FR, min_(uL - cL, K1u), max_(uR + cR, K5u), F);
+        return;
+    }
+    // Harten's smoothing with Harten-Hyman widths from the states beside
+    // each acoustic wave.
+    const T l1s = s1n * is1 - sqrt_(kc.gamma * p1 * is1);
+    const T l5s = s4n * is4 + sqrt_(kc.gamma * p4 * is4);
+    T e1 = abs_(K1u), e5 = abs_(K5u);
+    const T e2 = abs_(uT);
+    const T d1 = max_(T(0), max_(K1u - (uL - cL), l1s - K1u));
+    if (e1 < d1) e1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
+    const T d5 = max_(T(0), max_(K5u - l5s, (uR + cR) - K5u));
+    if (e5 < d5) e5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
+    const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
+    const T D0 = s1 + s2 + s5;
+    const T D1 = s1 * K1u + s2 * uT + s5 * K5u;
+    const T D2 = s1 * vT + s2 * vT + s3 + s5 * vT;
+    const T D3 = s1 * wT + s2 * wT + s4 + s5 * wT;
+    const T D4 = s1 * K1E + s2 * (T(0.5) * q2) + s3 * vT + s4 * wT + s5 * K5E;
+    F[0] = T(0.5) * (FL[0] + FR[0]) - T(0.5) * D0;
+    F[1] = T(0.5) * (FL[1] + FR[1]) - T(0.5) * D1;
+    F[2] = T(0.5) * (FL[2] + FR[2]) - T(0.5) * D2;
+    F[3] = T(0.5) * (FL[3] + FR[3]) - T(0.5) * D3;
+    F[4] = T(0.5) * (FL[4] + FR[4]) - T(0.5) * D4;
+}
+
+// ---------------------------------------------------------------------------
+// Conserved state of a primitive face value.
+template <class T, class P>
+__device__ __forceinline__ void cons(const T w[5], T u[5], T igm1) {
+    u[0] = w[0];
+    u[1] = w[0] * w[1];
+    u[2] = w[0] * w[2];
+    u[3] = w[0] * w[3];
+    u[4] = w[4] * igm1 + T(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+}
+
+// Flux difference F_d(W^-) - F_d(W^+) in direction D (compile time), with E^-
+// and E^+ the face energies.
+template <int D, class T>
+__device__ __forceinline__ void flux_diff(const T wm[5], T Em, const T wp[5], T Ep, T acc[5]) {
+    const T unm = wm[1 + D], unp = wp[1 + D];
+    const T mm = wm[0] * unm, mp = wp[0] * unp;
+    T fm[5], fp[5];
+    fm[0] = mm;
+    fm[1] = mm * wm[1];
+    fm[2] = mm * wm[2];
+    fm[3] = mm * wm[3];
+    fm[1 + D] = fm[1 + D] + wm[4];
+    fm[4] = (Em + wm[4]) * unm;
+    fp[0] = mp;
+    fp[1] = mp * wp[1];
+    fp[2] = mp * wp[2];
+    fp[3] = mp * wp[3];
+    fp[1 + D] = fp[1 + D] + wp[4];
+    fp[4] = (Ep + wp[4]) * unp;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = acc[q] + (fm[q] - fp[q]);
+}
+
+// Hancock half-step for the cell at plane index c (20x20 plane layout) of
+// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1, U0 the conserved
+// plane k.  fs[f] receives the conserved face states x-, x+, y-, y+, z-, z+.
+template <int MODE, class T, class P>
+__device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
+                                        const T* __restrict__ Wp, const T* __restrict__ U0,
+                                        int c, T half_lam, T igm1, const KConst<T, P>& kc,
+                                        T fs[6][5], uint32_t& st) {
+    T wc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) wc[q] = W0[q * kPlane + c];
+    T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T* lo = (d == 2) ? Wm + c : W0 + c - (d == 0 ? 1 : 20);
+        const T* hi = (d == 2) ? Wp + c : W0 + c + (d == 0 ? 1 : 20);
+        T wm[5], wp[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const T s = limit(wc[q] - lo[q * kPlane], hi[q * kPlane] - wc[q], kc);
+            wm[q] = wc[q] - T(0.5) * s;
+            wp[q] = wc[q] + T(0.5) * s;
+        }
+        cons<T, P>(wm, fs[2 * d], igm1);
+        cons<T, P>(wp, fs[2 * d + 1], igm1);
+        if (d == 0) flux_diff<0>(wm, fs[0][4], wp, fs[1][4], acc);
+        if (d == 1) flux_diff<1>(wm, fs[2][4], wp, fs[3][4], acc);
+        if (d == 2) flux_diff<2>(wm, fs[4][4], wp, fs[5][4], acc);
+    }
+    T du[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
+    bool ok = true;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const T r = fs[f][0] + du[0];
+        const T ir = rcp_(r);
+        const T p = pressure<MODE>(r, fs[f][1] + du[1], fs[f][2] + du[2], fs[f][3] + du[3],
+                                   fs[f][4] + du[4], ir, kc);
+        ok = ok && (r > T(0)) && (p > T(0));
+    }
+    if (ok) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
+    } else {
+        st |= GAMER_ST_PREDICTOR_FALLBACK;
+        if (kc.pfb == 0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const T u = U0[q * kPlane + c];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) fs[f][q] = u;
+            }
+        }
+    }
+}
+
+// cells of the 20^3 tile that the stencil reads: at most one coordinate
+// outside [0,16), or two, both one cell outside.
+__device__ __forceinline__ bool is_read_cell(int i, int j, int k) {
+    const bool oi = (unsigned)i > 15u, oj = (unsigned)j > 15u, ok = (unsigned)k > 15u;
+    const int o = int(oi) + int(oj) + int(ok);
+    const bool ni = !oi || i == -1 || i == 16;
+    const bool nj = !oj || j == -1 || j == 16;
+    const bool nk = !ok || k == -1 || k == 16;
+    return o <= 1 || (o == 2 && ni && nj && nk);
+}
+
+// Conserved plane -> primitive plane (all 400 cells; the flag covers the read cells).
+template <int MODE, class T, class P>
+__device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W, int kp,
+                                              const KConst<T, P>& kc, uint32_t& st) {
+    for (int c = threadIdx.x; c < kPlane; c += kThreads) {
+        T u[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) u[q] = U[q * kPlane + c];
+        const T ir = rcp_(u[0]);
+        W[0 * kPlane + c] = u[0];
+        W[1 * kPlane + c] = u[1] * ir;
+        W[2 * kPlane + c] = u[2] * ir;
+        W[3 * kPlane + c] = u[3] * ir;
+        W[4 * kPlane + c] = pressure<MODE>(u[0], u[1], u[2], u[3], u[4], ir, kc);
+        const int i = c % 20 - 2, j = c / 20 - 2;
+        if (is_read_cell(i, j, kp)) {
+            bool fin = true;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fin = fin && finite_(u[q]);
+            if (!fin) st |= GAMER_ST_BAD_INPUT;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void issue_plane(Smem<T>& S, const T* gin, int kp) {
+    const int slot = (kp + 2) % 3;
+    constexpr uint32_t bytes = 5u * kPlane * sizeof(T);
+    mbar_arrive_expect_tx(&S.mbar[slot], bytes);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        bulk_copy_g2s(&S.raw[slot][q * kPlane], gin + (q * 20 + (kp + 2)) * kPlane,
+                      kPlane * sizeof(T), &S.mbar[slot]);
+}
+
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
+    hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
+                      typename Prec<MODE>::T* __restrict__ out,
+                      typename Prec<MODE>::T* __restrict__ face_flux,
+                      const double* __restrict__ dt, const double* __restrict__ dh,
+                      uint32_t* __restrict__ status, double* __restrict__ partials, int64_t N,
+                      KConst<typename Prec<MODE>::T, typename Prec<MODE>::P> kc) {
+    using T = typename Prec<MODE>::T;
+    extern __shared__ __align__(128) unsigned char smem_bytes[];
+    Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_bytes);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        for (int s = 0; s < 3; ++s) mbar_init(&S.mbar[s], 1);
+        mbar_init_fence();
+        S.abort = 0;
+    }
+    __syncthreads();
+    uint32_t parity = 0;   // bit s: phase parity expected next on slot s
+    uint32_t pending = 0;  // bit s: a copy into slot s was issued and not yet waited for
+
+    // owned interior columns: c0 = (tid % 16, tid / 16); c1 = 10 rows further
+    const int i0 = tid & 15, j0 = tid >> 4, j1 = j0 + 10;
+    const bool two = tid < 96;  // warps 0-2 own two columns
+    const int pc0 = (j0 + 2) * 20 + (i0 + 2);
+    const int pc1 = (j1 + 2) * 20 + (i0 + 2);
+    // face-slab cell of threads 96..159: side 0: i=-1, 1: i=16, 2: j=-1, 3: j=16
+    const int sl = tid - 96, side = sl >> 4, st_ = sl & 15;
+    const int si = (side == 0) ? -1 : (side == 1) ? 16 : st_;
+    const int sj = (side == 2) ? -1 : (side == 3) ? 16 : st_;
+    const int psl = (sj + 2) * 20 + (si + 2);
+
+    const T igm1 = T(1) / kc.gm1;
+
+    for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
+        const T* gin = in + g * 40000;
+        T* gout = out + g * 20480;
+        T* gff = face_flux ? face_flux + g * 7680 : nullptr;
+        const double dtg = dt[g], dhg = dh[g];
+        const T lam = static_cast<T>(dtg / dhg);
+        const T half_lam = T(0.5) * lam;
+        uint32_t st = 0;
+        if (tid == 0) {
+            S.status = 0;
+            if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0)) st |= GAMER_ST_BAD_INPUT;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_plane(S, gin, -2);
+            issue_plane(S, gin, -1);
+            issue_plane(S, gin, 0);
+        }
+        pending |= 7u;
+        // prologue: planes -2, -1, 0 -> primitives
+        bool timed_out = false;
+        for (int kp = -2; kp <= 0; ++kp) {
+            const int slot = (kp + 2) % 3;
+            if (!timed_out && mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
+                parity ^= 1u << slot;
+                pending &= ~(1u << slot);
+                convert_plane<MODE>(S.raw[slot], S.W[slot], kp, kc, st);
+            } else {
+                timed_out = true;
+            }
+        }
+        if (__syncthreads_or(timed_out)) goto abort_group;
+
+        {
+            // owner registers
+            T zp0[5], zp1[5], fzo0[5], fzo1[5], D0[5], D1[5], Uo0[5], Uo1[5];
+            double smax = 0.0, ssum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                zp0[q] = zp1[q] = fzo0[q] = fzo1[q] = D0[q] = D1[q] = Uo0[q] = Uo1[q] = T(0);
+            }
+
+            for (int k = -1; k <= 16; ++k) {
+                if (k <= 15) {
+                    if (tid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_plane(S, gin, k + 2);
+                    }
+                    pending |= 1u << ((k + 4) % 3);
+                }
+                const T* Wm = S.W[(k + 1) % 3];
+                const T* W0 = S.W[(k + 2) % 3];
+                const T* Wp = S.W[(k + 3) % 3];
+                const T* Uk = S.raw[(k + 2) % 3];
+                const bool inner = (k >= 0 && k <= 15);
+
+                // ---- phase A: half-step prediction of plane k
+                T zm0[5], zm1[5], zpn0[5], zpn1[5];
+                {
+                    T fs[6][5];
+                    predict<MODE>(Wm, W0, Wp, Uk, pc0, half_lam, igm1, kc, fs, st);
+                    if (inner) {
+                        const int p = j0 * 16 + i0;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            S.xm[q * kFaceStride + p] = fs[0][q];
+                            S.xp[q * kFaceStride + p] = fs[1][q];
+                            S.ym[q * kFaceStride + p] = fs[2][q];
+                            S.yp[q * kFaceStride + p] = fs[3][q];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        zm0[q] = fs[4][q];
+                        zpn0[q] = fs[5][q];
+                    }
+                }
+                if (two) {
+                    T fs[6][5];
+                    predict<MODE>(Wm, W0, Wp, Uk, pc1, half_lam, igm1, kc, fs, st);
+                    if (inner) {
+                        const int p = j1 * 16 + i0;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            S.xm[q * kFaceStride + p] = fs[0][q];
+                            S.xp[q * kFaceStride + p] = fs[1][q];
+                            S.ym[q * kFaceStride + p] = fs[2][q];
+                            S.yp[q * kFaceStride + p] = fs[3][q];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        zm1[q] = fs[4][q];
+                        zpn1[q] = fs[5][q];
+                    }
+                } else if (inner) {
+                    T fs[6][5];
+                    predict<MODE>(Wm, W0, Wp, Uk, psl, half_lam, igm1, kc, fs, st);
+                    const int p = kFaceStride - 16 + st_;
+                    if (side == 0) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) S.xp[q * kFaceStride + p] = fs[1][q];
+                    } else if (side == 1) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) S.xm[q * kFaceStride + p] = fs[0][q];
+                    } else if (side == 2) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) S.yp[q * kFaceStride + p] = fs[3][q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) S.ym[q * kFaceStride + p] = fs[2][q];
+                    }
+                }
+                __syncthreads();
+
+                // ---- phase B: Riemann solves
+                T fz0[5], fz1[5];
+                if (k >= 0) {
+                    // z faces k-1/2 of the owned columns: rotated (rho, m_z, m_x, m_y, E)
+                    {
+                        T L[5] = {zp0[0], zp0[3], zp0[1], zp0[2], zp0[4]};
+                        T R[5] = {zm0[0], zm0[3], zm0[1], zm0[2], zm0[4]};
+                        T F[5];
+                        roe_rot<MODE>(L, R, kc, F, st);
+                        fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
+                        if (gff && (k == 0 || k == 16)) {
+                            T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j0 * 16 + i0;
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) dst[q * 256] = fz0[q];
+                        }
+                    }
+                    if (two) {
+                        T L[5] = {zp1[0], zp1[3], zp1[1], zp1[2], zp1[4]};
+                        T R[5] = {zm1[0], zm1[3], zm1[1], zm1[2], zm1[4]};
+                        T F[5];
+                        roe_rot<MODE>(L, R, kc, F, st);
+                        fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
+                        if (gff && (k == 0 || k == 16)) {
+                            T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j1 * 16 + i0;
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) dst[q * 256] = fz1[q];
+                        }
+                    }
+                }
+                if (inner) {
+                    // x faces: item = j*17 + f (f: face between i = f-1 and f)
+                    // y faces: item = 272 + f*16 + i (f: face between j = f-1 and f)
+                    const int nxy = two ? 3 : 4;
+                    for (int r = 0; r < nxy; ++r) {
+                        const int it = two ? (r * 96 + tid) : (288 + r * 64 + (tid - 96));
+                        const bool isy = it >= 272;
+                        int lo, hi, a, b;  // left/right state offsets in the face arrays
+                        const T *LA, *RA;
+                        if (!isy) {
+                            const int j = it / 17, f = it - j * 17;
+                            lo = (f == 0) ? (256 + j) : (j * 16 + f - 1);
+                            hi = (f == 16) ? (256 + j) : (j * 16 + f);
+                            LA = S.xp;
+                            RA = S.xm;
+                            a = j;
+                            b = f;
+                        } else {
+                            const int y = it - 272, f = y >> 4, i = y & 15;
+                            lo = (f == 0) ? (256 + i) : ((f - 1) * 16 + i);
+                            hi = (f == 16) ? (256 + i) : (f * 16 + i);
+                            LA = S.yp;
+                            RA = S.ym;
+                            a = i;
+                            b = f;
+                        }
+                        // rotation: x -> (0,1,2,3,4); y -> (0,2,3,1,4)
+                        const int c1 = isy ? 2 : 1, c2 = isy ? 3 : 2, c3 = isy ? 1 : 3;
+                        T L[5], R[5], F[5];
+                        L[0] = LA[lo];
+                        L[1] = LA[c1 * kFaceStride + lo];
+                        L[2] = LA[c2 * kFaceStride + lo];
+                        L[3] = LA[c3 * kFaceStride + lo];
+                        L[4] = LA[4 * kFaceStride + lo];
+                        R[0] = RA[hi];
+                        R[1] = RA[c1 * kFaceStride + hi];
+                        R[2] = RA[c2 * kFaceStride + hi];
+                        R[3] = RA[c3 * kFaceStride + hi];
+                        R[4] = RA[4 * kFaceStride + hi];
+                        roe_rot<MODE>(L, R, kc, F, st);
+                        S.fxy[it] = F[0];
+                        S.fxy[c1 * kFluxStride + it] = F[1];
+                        S.fxy[c2 * kFluxStride + it] = F[2];
+                        S.fxy[c3 * kFluxStride + it] = F[3];
+                        S.fxy[4 * kFluxStride + it] = F[4];
+                        if (gff && (b == 0 || b == 16)) {
+                            // faces -x,+x: [v][k][j];  -y,+y: [v][k][i]
+                            const int face = (isy ? 2 : 0) + (b == 16 ? 1 : 0);
+                            T* dst = gff + face * 1280 + k * 16 + a;
+                            dst[0] = F[0];
+                            dst[c1 * 256] = F[1];
+                            dst[c2 * 256] = F[2];
+                            dst[c3 * 256] = F[3];
+                            dst[4 * 256] = F[4];
+                        }
+                    }
+                }
+                __syncthreads();
+
+                // ---- phase C: finish plane k-1, set up plane k, convert plane k+2
+                if (k >= 1) {
+                    const int kk = k - 1;
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cc == 1 && !two) break;
+                        const T* Uo = cc ? Uo1 : Uo0;
+                        const T* Dd = cc ? D1 : D0;
+                        const T* fo = cc ? fzo1 : fzo0;
+                        const T* fn = cc ? fz1 : fz0;
+                        const int jj = cc ? j1 : j0;
+                        T o[5];
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            o[q] = Uo[q] - lam * (Dd[q] + (fn[q] - fo[q]));
+                            gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
+                        }
+                        // epilogue: positivity flag, FP64 signal speed and sums
+                        const T ir = rcp_(o[0]);
+                        const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                        if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
+                        const T c2 = kc.gamma * p * ir;
+                        const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
+                        const T vmax = max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir));
+                        const double sp = static_cast<double>(vmax + cs);
+                        if (sp > smax) smax = sp;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) ssum[q] += static_cast<double>(o[q]);
+                    }
+                }
+                if (inner) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        const T* fq = S.fxy + q * kFluxStride;
+                        D0[q] = (fq[j0 * 17 + i0 + 1] - fq[j0 * 17 + i0]) +
+                                (fq[272 + (j0 + 1) * 16 + i0] - fq[272 + j0 * 16 + i0]);
+                        Uo0[q] = Uk[q * kPlane + pc0];
+                        fzo0[q] = fz0[q];
+                        if (two) {
+                            D1[q] = (fq[j1 * 17 + i0 + 1] - fq[j1 * 17 + i0]) +
+                                    (fq[272 + (j1 + 1) * 16 + i0] - fq[272 + j1 * 16 + i0]);
+                            Uo1[q] = Uk[q * kPlane + pc1];
+                            fzo1[q] = fz1[q];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    zp0[q] = zpn0[q];
+                    zp1[q] = zpn1[q];
+                }
+                if (k <= 15) {
+                    const int slot = (k + 4) % 3;  // slot of plane k+2
+                    if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
+                        parity ^= 1u << slot;
+                        pending &= ~(1u << slot);
+                        convert_plane<MODE>(S.raw[slot], S.W[slot], k + 2, kc, st);
+                    } else {
+                        timed_out = true;
+                    }
+                }
+                if (__syncthreads_or(timed_out)) goto abort_group;
+            }
+
+            // ---- group epilogue: reductions
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+#pragma unroll
+                for (int q = 0; q < 5; ++q) ssum[q] += __shfl_xor_sync(0xffffffffu, ssum[q], off);
+            }
+            const uint32_t wst = __reduce_or_sync(0xffffffffu, st);
+            if (lane == 0) {
+                S.red[warp][0] = smax;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) S.red[warp][1 + q] = ssum[q];
+                if (wst) atomicOr(&S.status, wst);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (partials) {
+                    double m = 0.0, s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                    for (int w = 0; w < kThreads / 32; ++w) {
+                        m = fmax(m, S.red[w][0]);
+                        for (int q = 0; q < 5; ++q) s[q] += S.red[w][1 + q];
+                    }
+                    partials[g * 6] = m;
+                    for (int q = 0; q < 5; ++q) partials[g * 6 + 1 + q] = s[q];
+                }
+                if (status) status[g] = S.status;
+            }
+            __syncthreads();
+        }
+        continue;
+
+    abort_group:
+        // A bulk copy did not complete in time.  Wait (bounded) for every copy
+        // still in flight so none lands after the CTA exits, flag the group and
+        // stop this CTA.
+        if (tid == 0) {
+            for (int s = 0; s < 3; ++s)
+                if (pending & (1u << s)) mbar_wait(&S.mbar[s], (parity >> s) & 1u);
+            if (status) status[g] = GAMER_ST_INTERNAL_TIMEOUT;
+        }
+        return;
+    }
+}
+
+}  // namespace gamer

@@ -1,0 +1,11 @@
+// hydro_mixed.cu -- C-ABI entry point gamer_hydro_advance_mixed (one translation
+// unit per precision mode so the three instantiations compile in parallel).
+#include "hydro_launch.cuh"
+
+extern "C" int gamer_hydro_advance_mixed(const float* in, float* out, float* face_flux,
+                                      const double* dt, const double* dh, uint32_t* status,
+                                      double* partials, int64_t N, const gh_params* p,
+                                      void* stream) {
+    return gamer::hydro_advance<GAMER_MODE_MIXED>(in, out, face_flux, dt, dh, status, partials, N, p,
+                                          stream);
+}

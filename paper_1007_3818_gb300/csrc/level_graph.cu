@@ -1,0 +1,121 @@
+// level_graph.cu -- one CUDA graph for the device-resident step of a uniform
+// level: ghost fill -> MUSCL-Hancock/Roe step -> dt / conservation reduction
+// (whose per-group dt feeds the next step).  A graph advances level_a into
+// level_b; the caller alternates it with the graph of the swapped buffers, so
+// a run of steps needs no host involvement and no per-kernel launch overhead.
+#include <cuda_runtime.h>
+
+#include <new>
+
+#include "abi_common.h"
+#include "gamer_gb300.h"
+
+extern "C" int gamer_hydro_advance_f32(const float*, float*, float*, const double*, const double*,
+                                       uint32_t*, double*, int64_t, const gh_params*, void*);
+extern "C" int gamer_hydro_advance_mixed(const float*, float*, float*, const double*,
+                                         const double*, uint32_t*, double*, int64_t,
+                                         const gh_params*, void*);
+extern "C" int gamer_hydro_advance_f64(const double*, double*, double*, const double*,
+                                       const double*, uint32_t*, double*, int64_t,
+                                       const gh_params*, void*);
+
+struct gamer_level_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int enqueue_step(int mode, const void* cur, void* nxt, void* tiles, void* ff, double* dt_group,
+                 const double* dh_group, uint32_t* status, double* partials, int gx, int gy,
+                 int gz, int bc, const gh_params* p, const double* dh_level, double* dt_level,
+                 double* totals, void* ws, size_t ws_bytes, cudaStream_t s) {
+    const int64_t G = int64_t(gx) * gy * gz;
+    int rc;
+    if (mode == GAMER_MODE_F64)
+        rc = gamer_fill_ghosts_uniform_f64((const double*)cur, (double*)tiles, gx, gy, gz, bc, s);
+    else
+        rc = gamer_fill_ghosts_uniform_f32((const float*)cur, (float*)tiles, gx, gy, gz, bc, s);
+    if (rc != GAMER_OK) return rc;
+    if (mode == GAMER_MODE_F32)
+        rc = gamer_hydro_advance_f32((const float*)tiles, (float*)nxt, (float*)ff, dt_group,
+                                     dh_group, status, partials, G, p, s);
+    else if (mode == GAMER_MODE_MIXED)
+        rc = gamer_hydro_advance_mixed((const float*)tiles, (float*)nxt, (float*)ff, dt_group,
+                                       dh_group, status, partials, G, p, s);
+    else
+        rc = gamer_hydro_advance_f64((const double*)tiles, (double*)nxt, (double*)ff, dt_group,
+                                     dh_group, status, partials, G, p, s);
+    if (rc != GAMER_OK) return rc;
+    return gamer_hydro_dt(partials, G, nullptr, 1, dh_level, p->cfl, dt_level, totals, dt_group,
+                          ws, ws_bytes, s);
+}
+
+}  // namespace
+
+extern "C" int gamer_level_graph_create(int32_t mode, void* level_a, void* level_b, void* tiles,
+                                        void* face_flux, double* dt_group,
+                                        const double* dh_group, uint32_t* status,
+                                        double* partials, int32_t gx, int32_t gy, int32_t gz,
+                                        int32_t bc, const gh_params* p, const double* dh_level,
+                                        double* dt_level, double* totals, void* workspace,
+                                        size_t workspace_bytes, gamer_level_graph** out) {
+    using namespace gamer;
+    if (!out) return GAMER_E_NULL;
+    *out = nullptr;
+    if (mode < 0 || mode > 2 || gx < 1 || gy < 1 || gz < 1) return GAMER_E_PARAM;
+    int rc = check_params(p);
+    if (rc != GAMER_OK) return rc;
+    if (!(std::isfinite(p->cfl) && p->cfl > 0.0)) return GAMER_E_PARAM;
+    if (!level_a || !level_b || !tiles || !dt_group || !dh_group || !partials || !dh_level ||
+        !dt_level)
+        return GAMER_E_NULL;
+    const DeviceInfo d = current_device();
+    if (d.status != GAMER_OK) return d.status;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GAMER_E_CUDA;
+    gamer_level_graph* h = new (std::nothrow) gamer_level_graph();
+    if (!h) {
+        cudaStreamDestroy(s);
+        return GAMER_E_CUDA;
+    }
+    rc = GAMER_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = GAMER_E_CUDA;
+    } else {
+        rc = enqueue_step(mode, level_a, level_b, tiles, face_flux, dt_group, dh_group, status,
+                          partials, gx, gy, gz, bc, p, dh_level, dt_level, totals, workspace,
+                          workspace_bytes, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (rc == GAMER_OK && e != cudaSuccess) rc = GAMER_E_CUDA;
+        h->graph = g;
+        if (rc == GAMER_OK && cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess)
+            rc = GAMER_E_CUDA;
+    }
+    cudaStreamDestroy(s);
+    if (rc != GAMER_OK) {
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        delete h;
+        cudaGetLastError();
+        return rc;
+    }
+    *out = h;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_level_graph_launch(gamer_level_graph* h, void* stream) {
+    if (!h || !h->exec) return GAMER_E_NULL;
+    return cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? GAMER_OK
+               : GAMER_E_CUDA;
+}
+
+extern "C" int gamer_level_graph_destroy(gamer_level_graph* h) {
+    if (!h) return GAMER_E_NULL;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    delete h;
+    return GAMER_OK;
+}

@@ -1,0 +1,310 @@
+"""Thin ctypes binding of ``libgamer_gb300.so`` (C ABI in ``include/gamer_gb300.h``).
+
+Argument marshalling only: every step of the hydro path runs in the library's
+CUDA kernels.  Functions keep the C names and take torch tensors (device
+memory) plus an optional CUDA stream (default: torch's current stream).  The
+library is loaded on first use; if it has not been built the call raises
+``GamerError`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgamer_gb300.so")
+
+GAMER_MODE_F32, GAMER_MODE_MIXED, GAMER_MODE_F64 = 0, 1, 2
+ST_PREDICTOR_FALLBACK, ST_HLLE_FALLBACK, ST_NONPOSITIVE_OUT = 0x1, 0x2, 0x4
+ST_BAD_INPUT, ST_INTERNAL_TIMEOUT = 0x8, 0x10
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GamerError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = strerror(code) if _lib is not None else f"error {code}"
+        super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
+
+
+class gh_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("limiter", ctypes.c_int32), ("predictor_fallback", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0):
+    return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback), (0, 0))
+
+
+def lib():
+    """Load the CUDA library (raises GamerError if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise GamerError(-4, f"{LIB_PATH} is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        for name in ("gamer_hydro_advance_f32", "gamer_hydro_advance_mixed",
+                     "gamer_hydro_advance_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(gh_params), vp]
+            f.restype = ctypes.c_int
+        for name in ("gamer_fill_ghosts_uniform_f32", "gamer_fill_ghosts_uniform_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, i32, i32, i32, i32, vp]
+            f.restype = ctypes.c_int
+        L.gamer_hydro_dt_workspace_bytes.argtypes = [i64, i32]
+        L.gamer_hydro_dt_workspace_bytes.restype = ctypes.c_size_t
+        L.gamer_hydro_dt.argtypes = [vp, i64, vp, i32, vp, d, vp, vp, vp, vp, ctypes.c_size_t,
+                                     vp]
+        L.gamer_hydro_dt.restype = ctypes.c_int
+        L.gamer_strerror.argtypes = [ctypes.c_int]
+        L.gamer_strerror.restype = ctypes.c_char_p
+        L.gamer_device_check.argtypes = []
+        L.gamer_device_check.restype = ctypes.c_int
+        L.gamer_version.argtypes = []
+        L.gamer_version.restype = ctypes.c_char_p
+        L.gamer_set_hydro_ctas_per_sm.argtypes = [i32, i32]
+        L.gamer_set_hydro_ctas_per_sm.restype = ctypes.c_int
+        L.gamer_microbench.argtypes = [i32, i64, vp, i64, P(d), vp]
+        L.gamer_microbench.restype = ctypes.c_int
+        L.gamer_level_graph_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32,
+                                               i32, P(gh_params), vp, vp, vp, vp,
+                                               ctypes.c_size_t, P(vp)]
+        L.gamer_level_graph_create.restype = ctypes.c_int
+        L.gamer_level_graph_launch.argtypes = [vp, vp]
+        L.gamer_level_graph_launch.restype = ctypes.c_int
+        L.gamer_level_graph_destroy.argtypes = [vp]
+        L.gamer_level_graph_destroy.restype = ctypes.c_int
+        L.gamer_pipeline_create.argtypes = [i32, i64, i32, P(vp)]
+        L.gamer_pipeline_create.restype = ctypes.c_int
+        L.gamer_pipeline_advance_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64,
+                                                  P(gh_params)]
+        L.gamer_pipeline_advance_host.restype = ctypes.c_int
+        L.gamer_pipeline_set_timeout.argtypes = [vp, d]
+        L.gamer_pipeline_set_timeout.restype = ctypes.c_int
+        L.gamer_pipeline_destroy.argtypes = [vp]
+        L.gamer_pipeline_destroy.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def strerror(code):
+    return lib().gamer_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise GamerError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, dtype=None, shape_tail=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise GamerError(-1, f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise GamerError(-2, f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise GamerError(-2, f"{name} must be {dtype}, got {t.dtype}")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise GamerError(-2, f"{name} has shape {tuple(t.shape)}, expected (N, {shape_tail})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_ADV = {GAMER_MODE_F32: "gamer_hydro_advance_f32", GAMER_MODE_MIXED: "gamer_hydro_advance_mixed",
+        GAMER_MODE_F64: "gamer_hydro_advance_f64"}
+
+
+def _advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream):
+    import torch
+    T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+    N = int(inp.shape[0])
+    args = [_ptr(inp, T, (5, 20, 20, 20), "in"), _ptr(out, T, (5, 16, 16, 16), "out"),
+            _ptr(face_flux, T, (6, 5, 16, 16), "face_flux"), _ptr(dt, torch.float64, (), "dt"),
+            _ptr(dh, torch.float64, (), "dh"), _ptr(status, torch.int32, (), "status"),
+            _ptr(partials, torch.float64, (6,), "partials")]
+    for t, nm in ((out, "out"), (face_flux, "face_flux"), (dt, "dt"), (dh, "dh"),
+                  (status, "status"), (partials, "partials")):
+        if t is not None and int(t.shape[0]) != N:
+            raise GamerError(-2, f"{nm} has {int(t.shape[0])} groups, in has {N}")
+    rc = getattr(lib(), _ADV[mode])(*args, N, ctypes.byref(params), _stream(stream))
+    _check(rc, _ADV[mode])
+
+
+def gamer_hydro_advance_f32(inp, out, face_flux, dt, dh, status, partials, params, stream=None):
+    """One step of N groups, FP32.  Tensors: in[N,5,20,20,20] f32, out[N,5,16,16,16]
+    f32, face_flux[N,6,5,16,16] f32 or None, dt/dh[N] f64, status[N] int32 or
+    None, partials[N,6] f64 or None; params from make_params()."""
+    _advance(GAMER_MODE_F32, inp, out, face_flux, dt, dh, status, partials, params, stream)
+
+
+def gamer_hydro_advance_mixed(inp, out, face_flux, dt, dh, status, partials, params, stream=None):
+    """As gamer_hydro_advance_f32 with FP64 pressure recovery."""
+    _advance(GAMER_MODE_MIXED, inp, out, face_flux, dt, dh, status, partials, params, stream)
+
+
+def gamer_hydro_advance_f64(inp, out, face_flux, dt, dh, status, partials, params, stream=None):
+    """As gamer_hydro_advance_f32 with float64 arrays and arithmetic."""
+    _advance(GAMER_MODE_F64, inp, out, face_flux, dt, dh, status, partials, params, stream)
+
+
+def hydro_advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream=None):
+    _advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream)
+
+
+def _fill(name, T, level, inp, gx, gy, gz, bc, stream):
+    G = gx * gy * gz
+    if int(level.shape[0]) != G or int(inp.shape[0]) != G:
+        raise GamerError(-2, f"{name}: level/in must hold gx*gy*gz = {G} groups")
+    rc = getattr(lib(), name)(_ptr(level, T, (5, 16, 16, 16), "level"),
+                              _ptr(inp, T, (5, 20, 20, 20), "in"), gx, gy, gz, bc, _stream(stream))
+    _check(rc, name)
+
+
+def gamer_fill_ghosts_uniform_f32(level, inp, gx, gy, gz, bc, stream=None):
+    import torch
+    _fill("gamer_fill_ghosts_uniform_f32", torch.float32, level, inp, gx, gy, gz, bc, stream)
+
+
+def gamer_fill_ghosts_uniform_f64(level, inp, gx, gy, gz, bc, stream=None):
+    import torch
+    _fill("gamer_fill_ghosts_uniform_f64", torch.float64, level, inp, gx, gy, gz, bc, stream)
+
+
+def gamer_hydro_dt_workspace_bytes(N, n_levels):
+    return int(lib().gamer_hydro_dt_workspace_bytes(int(N), int(n_levels)))
+
+
+def gamer_hydro_dt(partials, level, dh_level, cfl, dt_out, totals, dt_group, workspace,
+                   stream=None):
+    """dt per level, conservation totals and per-group dt (FP64) on the device.
+    workspace: a CUDA tensor of at least gamer_hydro_dt_workspace_bytes(N, L) bytes."""
+    import torch
+    N = int(partials.shape[0])
+    L = int(dh_level.shape[0])
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    rc = lib().gamer_hydro_dt(_ptr(partials, torch.float64, (6,), "partials"), N,
+                              _ptr(level, torch.int32, (), "level"), L,
+                              _ptr(dh_level, torch.float64, (), "dh_level"), float(cfl),
+                              _ptr(dt_out, torch.float64, (), "dt_out"),
+                              _ptr(totals, torch.float64, (), "totals"),
+                              _ptr(dt_group, torch.float64, (), "dt_group"),
+                              _ptr(workspace, None, None, "workspace"), ws_bytes, _stream(stream))
+    _check(rc, "gamer_hydro_dt")
+
+
+def gamer_device_check():
+    return int(lib().gamer_device_check())
+
+
+def gamer_version():
+    return lib().gamer_version().decode()
+
+
+def gamer_set_hydro_ctas_per_sm(mode, ctas_per_sm):
+    _check(lib().gamer_set_hydro_ctas_per_sm(int(mode), int(ctas_per_sm)),
+           "gamer_set_hydro_ctas_per_sm")
+
+
+def gamer_microbench(kind, iters, buf, n=0, stream=None):
+    """Launches one throughput probe; returns its operation / byte count."""
+    work = ctypes.c_double(0.0)
+    rc = lib().gamer_microbench(int(kind), int(iters), _ptr(buf, None, None, "buf"), int(n),
+                                ctypes.byref(work), _stream(stream))
+    _check(rc, "gamer_microbench")
+    return work.value
+
+
+class LevelGraph:
+    """gamer_level_graph_*: one device-resident uniform-level step (level_a ->
+    level_b) per launch.  Keeps references to the tensors it was captured with."""
+
+    def __init__(self, mode, level_a, level_b, tiles, face_flux, dt_group, dh_group, status,
+                 partials, gx, gy, gz, bc, params, dh_level, dt_level, totals, workspace):
+        self._keep = (level_a, level_b, tiles, face_flux, dt_group, dh_group, status, partials,
+                      dh_level, dt_level, totals, workspace, params)
+        h = ctypes.c_void_p()
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        ws_bytes = workspace.numel() * workspace.element_size()
+        rc = lib().gamer_level_graph_create(int(mode), p(level_a), p(level_b), p(tiles),
+                                            p(face_flux), p(dt_group), p(dh_group), p(status),
+                                            p(partials), gx, gy, gz, bc, ctypes.byref(params),
+                                            p(dh_level), p(dt_level), p(totals), p(workspace),
+                                            ws_bytes, ctypes.byref(h))
+        _check(rc, "gamer_level_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().gamer_level_graph_launch(self.handle, _stream(stream)),
+               "gamer_level_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().gamer_level_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """gamer_pipeline_*: host-resident batches streamed through the GPU."""
+
+    def __init__(self, mode, batch_groups, with_flux=True):
+        h = ctypes.c_void_p()
+        _check(lib().gamer_pipeline_create(int(mode), int(batch_groups), int(bool(with_flux)),
+                                           ctypes.byref(h)), "gamer_pipeline_create")
+        self.handle = h
+        self.mode = mode
+
+    def set_timeout(self, seconds):
+        _check(lib().gamer_pipeline_set_timeout(self.handle, float(seconds)),
+               "gamer_pipeline_set_timeout")
+
+    def advance_host(self, inp, out, face_flux, dt, dh, status, partials, params):
+        """Host (CPU, ideally pinned) tensors with the layouts of hydro_advance."""
+        import torch
+        T = torch.float64 if self.mode == GAMER_MODE_F64 else torch.float32
+        for t, nm, dtype in ((inp, "in", T), (out, "out", T), (face_flux, "face_flux", T),
+                             (dt, "dt", torch.float64), (dh, "dh", torch.float64),
+                             (status, "status", torch.int32), (partials, "partials", torch.float64)):
+            if t is None:
+                continue
+            if t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+                raise GamerError(-2, f"{nm} must be a contiguous host tensor of {dtype}")
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        rc = lib().gamer_pipeline_advance_host(self.handle, p(inp), p(out), p(face_flux), p(dt),
+                                               p(dh), p(status), p(partials), int(inp.shape[0]),
+                                               ctypes.byref(params))
+        _check(rc, "gamer_pipeline_advance_host")
+
+    def close(self):
+        if self.handle:
+            lib().gamer_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -241,3 +241,20 @@ def random_smooth_groups(N, seed=DEFAULT_SEED, gamma=5.0 / 3.0, base_n=64, sigma
     base = lognormal_base(base_n, seed + 3, gamma=gamma, sigma_ln=sigma_ln, vel_rms=vel_rms)
     origins = rng.integers(0, base_n, size=(N, 3))
     return window_tiles(base, origins)
+
+
+def stress_groups(N, seed=DEFAULT_SEED, gamma=1.4):
+    """White-noise stress tiles (not a physical workload): per-cell random
+    log-density in [-4, 0], velocities in [-3, 3], log-pressure in [-7, -2],
+    periodic ghosts of each tile.  Strong enough to fire both fallbacks."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((N, 5, 20, 20, 20))
+    idx = (np.arange(20) - 2) % 16
+    for t in range(N):
+        shape = (16, 16, 16)
+        rho = np.exp(rng.uniform(-4.0, 0.0, shape))
+        u, v, w = (rng.uniform(-3.0, 3.0, shape) for _ in range(3))
+        p = np.exp(rng.uniform(-7.0, -2.0, shape))
+        U = to_conserved(rho, u, v, w, p, gamma)
+        out[t] = U[:, idx[:, None, None], idx[None, :, None], idx[None, None, :]]
+    return out

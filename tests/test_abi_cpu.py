@@ -1,0 +1,134 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every symbol
+the public header declares, and rejects bad arguments on the host before any
+device work (these calls never reach a launch, so they run without a GPU)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1007_3818_gb300 import build as cuda_build
+from paper_1007_3818_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gamer_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return native.lib()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gamer_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared_functions()
+    for required in ("gamer_hydro_advance_f32", "gamer_hydro_advance_mixed",
+                     "gamer_hydro_advance_f64", "gamer_fill_ghosts_uniform_f32",
+                     "gamer_fill_ghosts_uniform_f64", "gamer_hydro_dt",
+                     "gamer_hydro_dt_workspace_bytes", "gamer_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_covers_codes(lib):
+    for code in range(0, -9, -1):
+        assert native.strerror(code) != "unknown error code"
+    assert native.strerror(-99) == "unknown error code"
+
+
+def test_version_string(lib):
+    assert "sm_103a" in native.gamer_version()
+
+
+P = ctypes.c_void_p
+FAKE = 0x7F0000000000  # never dereferenced: every call below fails validation first
+
+
+def _adv(lib, name, in_=FAKE, out=FAKE + (1 << 30), ff=None, dt=FAKE + (2 << 30),
+         dh=FAKE + (3 << 30), st=None, part=None, N=4, params=None):
+    if params is None:
+        params = native.make_params(1.4)
+    f = getattr(lib, name)
+    return f(P(in_) if in_ else None, P(out) if out else None, P(ff) if ff else None,
+             P(dt) if dt else None, P(dh) if dh else None, P(st) if st else None,
+             P(part) if part else None, N, ctypes.byref(params), None)
+
+
+@pytest.mark.parametrize("name", ["gamer_hydro_advance_f32", "gamer_hydro_advance_mixed",
+                                  "gamer_hydro_advance_f64"])
+def test_advance_rejects_bad_arguments(lib, name):
+    assert _adv(lib, name, N=-1) == -2
+    assert _adv(lib, name, N=0) == 0  # no-op, returns before touching the device
+    assert _adv(lib, name, in_=None) == -1
+    assert _adv(lib, name, dt=None) == -1
+    assert _adv(lib, name, params=native.make_params(1.0)) == -2
+    assert _adv(lib, name, params=native.make_params(float("nan"))) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, limiter=3)) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, predictor_fallback=2)) == -2
+    bad = native.make_params(1.4)
+    bad.reserved[0] = 1
+    assert _adv(lib, name, params=bad) == -2
+    assert _adv(lib, name, in_=FAKE + 8) == -3           # TMA source needs 16 B alignment
+    assert _adv(lib, name, dt=FAKE + (2 << 30) + 4) == -3
+    assert _adv(lib, name, out=FAKE + 64) == -6          # out inside in
+    assert _adv(lib, name, ff=FAKE + (1 << 30) + 128) == -6  # face flux inside out
+    f = getattr(lib, name)
+    assert f(P(FAKE), P(FAKE + (1 << 30)), None, P(FAKE + (2 << 30)), P(FAKE + (3 << 30)),
+             None, None, 4, None, None) == -1            # params NULL
+
+
+def test_fill_ghosts_rejects_bad_arguments(lib):
+    f = lib.gamer_fill_ghosts_uniform_f32
+    assert f(P(FAKE), P(FAKE + (1 << 30)), 2, 2, 2, 2, None) == -2     # bc
+    assert f(P(FAKE), P(FAKE + (1 << 30)), -1, 2, 2, 0, None) == -2
+    assert f(P(FAKE), P(FAKE + (1 << 30)), 0, 2, 2, 0, None) == 0      # empty level
+    assert f(None, P(FAKE + (1 << 30)), 2, 2, 2, 0, None) == -1
+    assert f(P(FAKE), P(FAKE + (1 << 30) + 4), 2, 2, 2, 0, None) == -3  # in not 16 B aligned
+    assert f(P(FAKE), P(FAKE + 1024), 2, 2, 2, 0, None) == -6
+
+
+def test_hydro_dt_rejects_bad_arguments(lib):
+    ws = native.gamer_hydro_dt_workspace_bytes(1000, 3)
+    assert ws >= 8 * (3 + 5)
+    assert native.gamer_hydro_dt_workspace_bytes(10, 0) == 0
+    assert native.gamer_hydro_dt_workspace_bytes(10, 65) == 0
+    f = lib.gamer_hydro_dt
+    a = [P(FAKE), 1000, None, 3, P(FAKE + (1 << 20)), 0.5, P(FAKE + (2 << 20)), None, None,
+         P(FAKE + (3 << 20)), ws, None]
+    b = list(a); b[3] = 0
+    assert f(*b) == -2
+    b = list(a); b[5] = -0.5
+    assert f(*b) == -2
+    b = list(a); b[10] = ws - 8
+    assert f(*b) == -7
+    b = list(a); b[9] = None
+    assert f(*b) == -7
+    b = list(a); b[0] = None
+    assert f(*b) == -1
+    b = list(a); b[0] = P(FAKE + 4)
+    assert f(*b) == -3
+
+
+def test_set_launch_shape_validation(lib):
+    assert lib.gamer_set_hydro_ctas_per_sm(3, 1) == -2
+    assert lib.gamer_set_hydro_ctas_per_sm(0, -1) == -2
+    assert lib.gamer_set_hydro_ctas_per_sm(0, 0) == 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(native, "_lib", None)
+    monkeypatch.setattr(native, "LIB_PATH", "/nonexistent/libgamer_gb300.so")
+    with pytest.raises(native.GamerError):
+        native.lib()

@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L1 per conserved field, sum|a-b|/sum|b|): FP64 <= 1e-12
+per step; FP32 and mixed <= 1e-5 after one step and <= 1e-4 after ten steps
+on smooth flows; face fluxes 10x looser (raw fluxes of nearly cancelling
+faces).  FP32 modes are compared with the oracle run on the same FP32-rounded
+input.  Integer outputs (status bits, ghost fill) are compared exactly.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import (TOL_F32_1, TOL_F32_10, TOL_F64, compare_step, flux_rel_l1, gpu_advance,
+                      host_input, rel_l1_fields, torch_dtype)
+from paper_1007_3818_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+F32, MIXED, F64 = 0, 1, 2
+MODES = [pytest.param(F32, TOL_F32_1, id="f32"), pytest.param(MIXED, TOL_F32_1, id="mixed"),
+         pytest.param(F64, TOL_F64, id="f64")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1007_3818_gb300 import native
+    assert native.gamer_device_check() == 0, native.strerror(native.gamer_device_check())
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode,tol", MODES)
+def test_random_smooth_groups(mode, tol):
+    tiles = wl.random_smooth_groups(7, seed=101, gamma=5 / 3)
+    compare_step(tiles, 2e-3, 1 / 256, 5 / 3, mode, tol)
+
+
+@pytest.mark.parametrize("mode,tol", MODES)
+def test_per_group_dt_dh(mode, tol):
+    """Groups of different AMR levels in one launch, each with its own dt, dh."""
+    tiles, level, dh_level = wl.amr_batch(counts=(3, 4, 5), seed=7, base_n=64)
+    dh = dh_level[level]
+    dt = 0.3 * dh / 4.0
+    compare_step(tiles, dt, dh, 5 / 3, mode, tol)
+
+
+@pytest.mark.parametrize("limiter", [1, 2])
+def test_other_limiters_f64(limiter):
+    tiles = wl.random_smooth_groups(3, seed=5, gamma=5 / 3)
+    compare_step(tiles, 2e-3, 1 / 256, 5 / 3, F64, TOL_F64, limiter=limiter)
+
+
+def _tube_tile(left, right, gamma):
+    U = wl.shock_tube_level(16, left, right, gamma, ny=16, nz=16)
+    return oracle.fill_ghosts_uniform(wl.level_to_groups(U), 1, 1, 1, 1)
+
+
+@pytest.mark.parametrize("pfb", [0, 1])
+def test_fallback_paths_f64(pfb):
+    """White-noise stress tiles and a strong double rarefaction: HLLE and
+    predictor fallbacks fire; status bits and state match the oracle."""
+    g = 1.4
+    tiles = np.concatenate([wl.stress_groups(3, seed=11, gamma=g),
+                            _tube_tile((1, -2, 0.4), (1, 2, 0.4), g)])
+    dt = 0.004
+    compare_step(tiles, dt, 1 / 16, g, F64, TOL_F64, predictor_fallback=pfb)
+    _, _, st, _ = gpu_advance(tiles, dt, 1 / 16, g, F64, predictor_fallback=pfb)
+    assert (st[:3] & 1).all() and (st & 2).all()
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED])
+def test_fallback_paths_fp32(mode):
+    """FP32 modes on the same stress tiles: the fallbacks fire and the state
+    stays close to the oracle (branch decisions may differ in a few cells, so
+    the bound is looser than the smooth-flow tolerance)."""
+    g = 1.4
+    tiles = host_input(wl.stress_groups(3, seed=11, gamma=g), mode)
+    out, ff, st, _ = gpu_advance(tiles, 0.004, 1 / 16, g, mode)
+    r_out, _, r_st, _ = oracle.advance_groups(tiles, 0.004, 1 / 16, gamma=g)
+    assert ((st & 3) == (r_st & 3)).all()
+    assert rel_l1_fields(out, r_out) <= 1e-3
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED, F64])
+def test_uniform_state_is_preserved_bitwise(mode):
+    g = 5 / 3
+    W = np.array([1.7, 0.4, -1.3, 0.25, 0.6])
+    U = oracle.cons(W, g)
+    if mode != F64:
+        U = U.astype(np.float32).astype(np.float64)
+    tiles = np.broadcast_to(U[None, :, None, None, None], (2, 5, 20, 20, 20)).copy()
+    out, ff, st, _ = gpu_advance(tiles, 1e-2, 1 / 64, g, mode)
+    assert np.array_equal(out, tiles[:, :, 2:18, 2:18, 2:18])
+    assert (st == 0).all()
+    for face in range(6):  # the same flux on every face of a given orientation
+        f = ff[:, face]
+        assert np.array_equal(f, np.broadcast_to(f[:, :, :1, :1], f.shape))
+
+
+@pytest.mark.parametrize("mode", [F32, F64])
+def test_unread_corner_cells_are_ignored(mode):
+    g = 5 / 3
+    tiles = host_input(wl.random_smooth_groups(2, seed=9, gamma=g), mode)
+    ref = gpu_advance(tiles, 2e-3, 1 / 256, g, mode)
+    idx = np.arange(-2, 18)
+    o = ((idx < 0) | (idx > 15)).astype(int)
+    d1 = (idx == -1) | (idx == 16)
+    cnt = o[:, None, None] + o[None, :, None] + o[None, None, :]
+    ok1 = lambda a: d1 | (o == 0)
+    deep = ok1(0)[:, None, None] & ok1(0)[None, :, None] & ok1(0)[None, None, :]
+    mask = (cnt == 3) | ((cnt == 2) & ~deep)
+    bad = tiles.copy()
+    bad[:, :, mask] = np.nan
+    got = gpu_advance(bad, 2e-3, 1 / 256, g, mode)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_nonfinite_read_input_sets_status():
+    g = 5 / 3
+    tiles = wl.random_smooth_groups(3, seed=4, gamma=g)
+    tiles[1, 2, 0, 10, 10] = np.inf   # face ghost at depth 2 (k = -2), read
+    _, _, st, _ = gpu_advance(tiles, 1e-3, 1 / 256, g, F32)
+    assert st[1] & 8 and not st[0] & 8 and not st[2] & 8
+
+
+def test_zero_groups_is_a_noop():
+    import torch
+    from paper_1007_3818_gb300 import native
+    e = torch.empty((0, 5, 20, 20, 20), device="cuda")
+    o = torch.empty((0, 5, 16, 16, 16), device="cuda")
+    z = torch.empty((0,), device="cuda", dtype=torch.float64)
+    native.gamer_hydro_advance_f32(e, o, None, z, z, None, None, native.make_params(1.4))
+
+
+def test_many_groups_ragged_tail_sampled():
+    """More groups than one wave of the persistent grid, with a ragged tail;
+    sampled groups compared with the oracle (F32)."""
+    g = 5 / 3
+    N = 2 * 152 * 2 + 37
+    tiles = host_input(wl.random_smooth_groups(N, seed=12, gamma=g), F32)
+    out, ff, st, part = gpu_advance(tiles, 2e-3, 1 / 256, g, F32)
+    sample = np.unique(np.r_[0, 1, 303, 304, 607, 608, N - 2, N - 1,
+                             np.random.default_rng(0).integers(0, N, 8)])
+    r_out, r_ff, r_st, r_part = oracle.advance_groups(tiles[sample], 2e-3, 1 / 256, gamma=g)
+    assert rel_l1_fields(out[sample], r_out) <= TOL_F32_1
+    assert flux_rel_l1(ff[sample], r_ff) <= 10 * TOL_F32_1
+    assert np.array_equal(st[sample], r_st)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("T", ["f32", "f64"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fill_ghosts_bit_exact(T, bc):
+    import torch
+    from paper_1007_3818_gb300 import native
+    gx, gy, gz = 3, 2, 4
+    rng = np.random.default_rng(bc)
+    level = rng.standard_normal((gx * gy * gz, 5, 16, 16, 16))
+    if T == "f32":
+        level = level.astype(np.float32).astype(np.float64)
+    ref = oracle.fill_ghosts_uniform(level, gx, gy, gz, bc)
+    tdt = torch.float32 if T == "f32" else torch.float64
+    d_level = torch.from_numpy(level).to("cuda", tdt)
+    d_in = torch.full((gx * gy * gz, 5, 20, 20, 20), float("nan"), device="cuda", dtype=tdt)
+    fn = native.gamer_fill_ghosts_uniform_f32 if T == "f32" else native.gamer_fill_ghosts_uniform_f64
+    fn(d_level, d_in, gx, gy, gz, bc)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_in.double().cpu().numpy(), ref)
+
+
+def test_hydro_dt_matches_oracle():
+    import torch
+    from paper_1007_3818_gb300 import native
+    rng = np.random.default_rng(3)
+    N, L = 5000, 3
+    part = np.column_stack([rng.uniform(0.1, 3.0, N), rng.standard_normal((N, 5))])
+    level = rng.integers(0, L, N).astype(np.int32)
+    dh_level = np.array([1 / 256, 1 / 512, 1 / 1024])
+    r_dt, r_tot = oracle.hydro_dt(part, dh_level, 0.5, level=level)
+    d = lambda a, t=torch.float64: torch.as_tensor(a, device="cuda", dtype=t)
+    dt_out = torch.zeros(L, device="cuda", dtype=torch.float64)
+    tot = torch.zeros(5, device="cuda", dtype=torch.float64)
+    dt_group = torch.zeros(N, device="cuda", dtype=torch.float64)
+    ws = torch.empty(native.gamer_hydro_dt_workspace_bytes(N, L), device="cuda", dtype=torch.uint8)
+    native.gamer_hydro_dt(d(part), d(level, torch.int32), d(dh_level), 0.5, dt_out, tot, dt_group,
+                          ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(dt_out.cpu().numpy(), r_dt)  # max and one division: exact
+    assert np.allclose(tot.cpu().numpy(), r_tot, rtol=1e-13, atol=1e-13 * np.abs(part).sum())
+    assert np.array_equal(dt_group.cpu().numpy(), r_dt[level])
+
+
+# --------------------------------------------------------------------------
+def _gpu_level_steps(U_level, gx, gy, gz, bc, dts, dh, gamma, mode):
+    """Device-resident uniform-level steps: ghost fill -> advance, dt given."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    T = torch_dtype(mode)
+    G = gx * gy * gz
+    cur = torch.from_numpy(wl.level_to_groups(U_level)).to("cuda", T)
+    nxt = torch.empty_like(cur)
+    tiles = torch.empty((G, 5, 20, 20, 20), device="cuda", dtype=T)
+    dh_t = torch.full((G,), dh, device="cuda", dtype=torch.float64)
+    part = torch.empty((G, 6), device="cuda", dtype=torch.float64)
+    fill = native.gamer_fill_ghosts_uniform_f64 if mode == F64 else native.gamer_fill_ghosts_uniform_f32
+    params = native.make_params(gamma)
+    states = []
+    for dt in dts:
+        fill(cur, tiles, gx, gy, gz, bc)
+        dt_t = torch.full((G,), dt, device="cuda", dtype=torch.float64)
+        native.hydro_advance(mode, tiles, nxt, None, dt_t, dh_t, None, part, params)
+        cur, nxt = nxt, cur
+        states.append(cur.double().cpu().numpy())
+    return states
+
+
+def _oracle_level_steps(U_level, gx, gy, gz, bc, nsteps, dh, gamma, cfl=0.5):
+    G = wl.level_to_groups(U_level)
+    states, dts = [], []
+    for _ in range(nsteps):
+        tiles = oracle.fill_ghosts_uniform(G, gx, gy, gz, bc)
+        _, _, _, part = oracle.advance_groups(tiles, 0.0, dh, gamma=gamma, want_flux=False)
+        dt = oracle.hydro_dt(part, [dh], cfl)[0][0]
+        G, _, _, _ = oracle.advance_groups(tiles, dt, dh, gamma=gamma, want_flux=False)
+        states.append(G)
+        dts.append(dt)
+    return states, dts
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED, F64])
+def test_periodic_level_ten_steps(mode):
+    """Config 2 recipe at 64^3 (4^3 groups): ten steps with the oracle's dt
+    sequence; FP64 per step <= 1e-12, FP32 after 1 step <= 1e-5 and after 10
+    steps <= 1e-4."""
+    g = 5 / 3
+    U = wl.fourier_level(n=64, seed=1007, gamma=g)
+    if mode != F64:
+        U = U.astype(np.float32).astype(np.float64)
+    ref, dts = _oracle_level_steps(U, 4, 4, 4, 0, 10, 1 / 64, g)
+    got = _gpu_level_steps(U, 4, 4, 4, 0, dts, 1 / 64, g, mode)
+    if mode == F64:
+        # per-step tolerance: restart each step from the oracle state
+        for s in range(10):
+            prev = U if s == 0 else wl.groups_to_level(ref[s - 1], 4, 4, 4)
+            one = _gpu_level_steps(prev, 4, 4, 4, 0, [dts[s]], 1 / 64, g, mode)[0]
+            assert rel_l1_fields(one, ref[s]) <= TOL_F64, s
+    else:
+        assert rel_l1_fields(got[0], ref[0]) <= TOL_F32_1
+        assert rel_l1_fields(got[9], ref[9]) <= TOL_F32_10
+
+
+@pytest.mark.parametrize("mode", [F32, F64])
+def test_sod_single_group_ten_steps(mode):
+    """Config 1: Sod in one group, zero-gradient ghosts refilled on the device
+    each step, oracle dt sequence (CFL 0.5)."""
+    g = 1.4
+    U = wl.sod_group(g)
+    ref, dts = _oracle_level_steps(U, 1, 1, 1, 1, 10, 1 / 16, g)
+    got = _gpu_level_steps(U, 1, 1, 1, 1, dts, 1 / 16, g, mode)
+    tol = TOL_F64 * 10 if mode == F64 else TOL_F32_10
+    assert rel_l1_fields(got[-1], ref[-1]) <= tol
+    # transverse momenta stay exactly zero
+    assert not got[-1][:, 2].any() and not got[-1][:, 3].any()
