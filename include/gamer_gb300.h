@@ -205,8 +205,11 @@ int gamer_device_check(void);
 const char* gamer_version(void);
 
 /* Launch shape of gamer_hydro_advance_<mode> (mode = GAMER_MODE_*): CTAs per
- * SM of the persistent grid, 0 = as many as fit (default).  Used by the
- * autotuner; process-wide setting. */
+ * SM of the persistent grid.  The FP32 modes come in two builds, sized for 2
+ * CTAs per SM (no register spills) and for 3 (more warps per SM); 2 selects
+ * the first, 0 or 3 the second (default).  FP64 always runs 1 CTA per SM.
+ * Larger values are capped at what fits.  Used by the autotuner;
+ * process-wide setting. */
 int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
 
 /* Throughput probes for the roofline denominators (not part of the scheme).

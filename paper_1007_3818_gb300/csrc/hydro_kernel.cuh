@@ -2,27 +2,32 @@
 //
 // Paper Sec. 2: spatial data reconstruction, half-step prediction, Riemann
 // solver (Roe), full-step update; unsplit; five-point stencil per direction.
-// The scheme details follow the readings listed with the C ABI (primitive
-// reconstruction, van Leer / minmod / MC limiters, conservative Hancock
-// half-step with a cell-average fallback, Roe flux with Harten's smoothing of
-// |lambda| on the acoustic waves using Harten-Hyman widths from the Roe
-// intermediate states, HLLE with Einfeldt speeds as fallback).
+// Scheme details (the readings the C ABI documents): primitive reconstruction
+// with a van Leer / minmod / MC limiter, conservative Hancock half-step with a
+// cell-average fallback, Roe flux with Harten's smoothing of |lambda| on the
+// acoustic waves using Harten-Hyman widths from the Roe intermediate states,
+// HLLE with Einfeldt speeds as fallback.
 //
 // GB300 design (one CTA of 160 threads per patch group, persistent over the
-// batch, 2 CTAs per SM in FP32):
+// batch):
 //  * z-marching: the 20^3 input arrives one z-plane (5 x 20 x 20 values) at a
 //    time through the TMA engine (cp.async.bulk, 5 x 1600 B per plane in FP32)
-//    into a 3-slot shared ring, prefetched one iteration ahead, and is
-//    converted once per cell into a 3-plane ring of primitives.
+//    into a 2-slot shared ring; the copy of plane k+2 is issued as soon as
+//    plane k has been read (after phase A) and lands while phase B runs.  Each
+//    plane is converted once per cell into a 3-plane ring of primitives.
 //  * per plane k: phase A predicts the 320 cells of the plane (16^2 interior +
-//    4 x 16 face-slab cells) -- two per thread; phase B solves the 800 Riemann
-//    problems whose fluxes touch the plane (272 x-faces, 272 y-faces from
-//    shared memory, 256 z-faces from registers) -- exactly five per thread;
-//    phase C finishes the update of plane k-1 and converts plane k+2.
+//    4 x 16 face-slab cells), two per thread; phase B solves the 800 Riemann
+//    problems of the plane (272 x-faces and 272 y-faces from shared memory,
+//    256 z-faces from registers), exactly five per thread; phase C finishes
+//    plane k-1 and converts plane k+2.
 //  * each interior column (i,j) has an owner thread that keeps its z-face
-//    states, z-fluxes, the x/y flux divergence and the old state in registers,
-//    so nothing of the z direction goes through shared memory.
-//  * the epilogue reductions (max signal speed, conserved sums) are FP64.
+//    state, z-flux and partial update in registers, so nothing of the z
+//    direction goes through shared memory.  The two half-warps of a warp own
+//    rows j and j+4, 80 floats apart in a 20-wide plane, so every plane access
+//    of a warp hits 32 distinct banks; the 16-wide face and flux arrays store
+//    row j at j ^ ((j >> 2) & 1) for the same reason.
+//  * epilogue sums are compensated (TwoSum) per thread and reduced in FP64
+//    across threads; FP32 modes issue no FP64 instruction per cell.
 #pragma once
 
 #include <cstdint>
@@ -45,14 +50,13 @@ template <> struct Prec<GAMER_MODE_F64> { using T = double; using P = double; };
 
 template <class T>
 struct alignas(16) Smem {
-    T raw[3][5 * kPlane];  // TMA ring of conserved input planes
+    T raw[2][5 * kPlane];  // TMA ring of conserved input planes
     T W[3][5 * kPlane];    // primitive planes
     T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
     T fxy[5 * kFluxStride];  // x- and y-face fluxes of the current plane
     double red[kThreads / 32][6];
-    uint64_t mbar[3];
+    uint64_t mbar[2];
     uint32_t status;
-    int32_t abort;
 };
 
 template <class T, class P>
@@ -61,6 +65,9 @@ struct KConst {
     P gm1p;
     int limiter, pfb;
 };
+
+// row slot of a 16-wide face / flux array (see the bank note above)
+__device__ __forceinline__ int frow(int j) { return j ^ ((j >> 2) & 1); }
 
 // ---------------------------------------------------------------------------
 // Pressure from a conserved state, given 1/rho in T.  MIXED recovers it in
@@ -76,6 +83,18 @@ __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KC
         return static_cast<T>(kc.gm1p * (static_cast<double>(E) - ke));
     } else {
         return kc.gm1 * (E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
+    }
+}
+
+// rho > 0 and p > 0, tested as rho > 0 and rho E - |m|^2 / 2 > 0 (no division);
+// MIXED evaluates the difference in FP64.
+template <int MODE, class T>
+__device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
+    if constexpr (MODE == GAMER_MODE_MIXED) {
+        const double a = m1, b = m2, c = m3;
+        return r > T(0) && (double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0;
+    } else {
+        return r > T(0) && (r * E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3)) > T(0);
     }
 }
 
@@ -98,8 +117,8 @@ __device__ __forceinline__ T limit(T a, T b, const KConst<T, P>& kc) {
 // ---------------------------------------------------------------------------
 // HLLE flux (rotated frame) with Einfeldt speed bounds.
 template <class T>
-__device__ __forceinline__ void hlle_rot(const T L[5], const T R[5], const T FL[5], const T FR[5],
-                                      T sl, T sr, T F[5]) {
+__device__ __forceinline__ void hlle_rot(const T L[5], const T R[5], const T FL[5],
+                                         const T FR[5], T sl, T sr, T F[5]) {
     const T bm = min_(sl, T(0));
     const T bp = max_(sr, T(0));
     const T inv = rcp_(bp - bm);
@@ -198,7 +217,7 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
 
 // ---------------------------------------------------------------------------
 // Conserved state of a primitive face value.
-template <class T, class P>
+template <class T>
 __device__ __forceinline__ void cons(const T w[5], T u[5], T igm1) {
     u[0] = w[0];
     u[1] = w[0] * w[1];
@@ -208,7 +227,7 @@ __device__ __forceinline__ void cons(const T w[5], T u[5], T igm1) {
 }
 
 // Flux difference F_d(W^-) - F_d(W^+) in direction D (compile time), with E^-
-// and E^+ the face energies.
+// and E^+ the face energies, accumulated into acc.
 template <int D, class T>
 __device__ __forceinline__ void flux_diff(const T wm[5], T Em, const T wp[5], T Ep, T acc[5]) {
     const T unm = wm[1 + D], unp = wp[1 + D];
@@ -231,12 +250,13 @@ __device__ __forceinline__ void flux_diff(const T wm[5], T Em, const T wp[5], T 
 }
 
 // Hancock half-step for the cell at plane index c (20x20 plane layout) of
-// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1, U0 the conserved
-// plane k.  fs[f] receives the conserved face states x-, x+, y-, y+, z-, z+.
+// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1; uc the cell's
+// conserved state.  fs[f] receives the conserved face states x-, x+, y-, y+,
+// z-, z+.
 template <int MODE, class T, class P>
 __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
-                                        const T* __restrict__ Wp, const T* __restrict__ U0,
-                                        int c, T half_lam, T igm1, const KConst<T, P>& kc,
+                                        const T* __restrict__ Wp, const T uc[5], int c,
+                                        T half_lam, T igm1, const KConst<T, P>& kc,
                                         T fs[6][5], uint32_t& st) {
     T wc[5];
 #pragma unroll
@@ -253,8 +273,8 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
             wm[q] = wc[q] - T(0.5) * s;
             wp[q] = wc[q] + T(0.5) * s;
         }
-        cons<T, P>(wm, fs[2 * d], igm1);
-        cons<T, P>(wp, fs[2 * d + 1], igm1);
+        cons<T>(wm, fs[2 * d], igm1);
+        cons<T>(wp, fs[2 * d + 1], igm1);
         if (d == 0) flux_diff<0>(wm, fs[0][4], wp, fs[1][4], acc);
         if (d == 1) flux_diff<1>(wm, fs[2][4], wp, fs[3][4], acc);
         if (d == 2) flux_diff<2>(wm, fs[4][4], wp, fs[5][4], acc);
@@ -264,13 +284,9 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
     for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
     bool ok = true;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        const T r = fs[f][0] + du[0];
-        const T ir = rcp_(r);
-        const T p = pressure<MODE>(r, fs[f][1] + du[1], fs[f][2] + du[2], fs[f][3] + du[3],
-                                   fs[f][4] + du[4], ir, kc);
-        ok = ok && (r > T(0)) && (p > T(0));
-    }
+    for (int f = 0; f < 6; ++f)
+        ok = ok && admissible<MODE>(fs[f][0] + du[0], fs[f][1] + du[1], fs[f][2] + du[2],
+                                    fs[f][3] + du[3], fs[f][4] + du[4]);
     if (ok) {
 #pragma unroll
         for (int f = 0; f < 6; ++f)
@@ -280,11 +296,9 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
         st |= GAMER_ST_PREDICTOR_FALLBACK;
         if (kc.pfb == 0) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const T u = U0[q * kPlane + c];
+            for (int f = 0; f < 6; ++f)
 #pragma unroll
-                for (int f = 0; f < 6; ++f) fs[f][q] = u;
-            }
+                for (int q = 0; q < 5; ++q) fs[f][q] = uc[q];
         }
     }
 }
@@ -326,8 +340,9 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
 
 template <class T>
 __device__ __forceinline__ void issue_plane(Smem<T>& S, const T* gin, int kp) {
-    const int slot = (kp + 2) % 3;
+    const int slot = (kp + 2) & 1;
     constexpr uint32_t bytes = 5u * kPlane * sizeof(T);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive_expect_tx(&S.mbar[slot], bytes);
 #pragma unroll
     for (int q = 0; q < 5; ++q)
@@ -335,9 +350,32 @@ __device__ __forceinline__ void issue_plane(Smem<T>& S, const T* gin, int kp) {
                       kPlane * sizeof(T), &S.mbar[slot]);
 }
 
+// Accumulator of the per-group conserved sums: FP64 in FP64 mode; in FP32
+// modes a compensated (hi, lo) float pair per thread (TwoSum), exact to about
+// 2^-48 relative for the few dozen terms one thread adds.
+template <class T> struct SumAcc;
+template <> struct SumAcc<double> {
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    __device__ __forceinline__ void add(int q, double x) { s[q] += x; }
+    __device__ __forceinline__ double get(int q) const { return s[q]; }
+};
+template <> struct SumAcc<float> {
+    float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(int q, float x) {
+        const float s = hi[q] + x;
+        const float bp = s - hi[q];
+        const float err = (hi[q] - (s - bp)) + (x - bp);
+        hi[q] = s;
+        lo[q] += err;
+    }
+    __device__ __forceinline__ double get(int q) const { return double(hi[q]) + double(lo[q]); }
+};
+
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
+// MINB: CTAs per SM the register budget is sized for (launch bounds); the
+// launcher picks the variant (2: no spills, 3: more warps per SM).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
                       typename Prec<MODE>::T* __restrict__ face_flux,
@@ -351,19 +389,23 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
     const int lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < 3; ++s) mbar_init(&S.mbar[s], 1);
+        for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], 1);
         mbar_init_fence();
-        S.abort = 0;
     }
     __syncthreads();
     uint32_t parity = 0;   // bit s: phase parity expected next on slot s
     uint32_t pending = 0;  // bit s: a copy into slot s was issued and not yet waited for
 
-    // owned interior columns: c0 = (tid % 16, tid / 16); c1 = 10 rows further
-    const int i0 = tid & 15, j0 = tid >> 4, j1 = j0 + 10;
-    const bool two = tid < 96;  // warps 0-2 own two columns
+    // owned interior columns: a warp owns a row pair (jA, jA + 4), lane -> i;
+    // warps 0-4 own pairs 0-4 (c0), warps 0-2 also pairs 5-7 (c1)
+    const bool two = tid < 96;
+    const int i0 = lane & 15, hb = (lane >> 4) * 4;
+    const int pa = warp, pb = warp + 5;
+    const int j0 = (pa & 3) + ((pa >> 2) << 3) + hb;
+    const int j1 = (pb & 3) + ((pb >> 2) << 3) + hb;
     const int pc0 = (j0 + 2) * 20 + (i0 + 2);
     const int pc1 = (j1 + 2) * 20 + (i0 + 2);
+    const int fa0 = frow(j0) * 16 + i0, fa1 = frow(j1) * 16 + i0;
     // face-slab cell of threads 96..159: side 0: i=-1, 1: i=16, 2: j=-1, 3: j=16
     const int sl = tid - 96, side = sl >> 4, st_ = sl & 15;
     const int si = (side == 0) ? -1 : (side == 1) ? 16 : st_;
@@ -382,21 +424,29 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
         uint32_t st = 0;
         if (tid == 0) {
             S.status = 0;
-            if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0)) st |= GAMER_ST_BAD_INPUT;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0))
+                st |= GAMER_ST_BAD_INPUT;
             issue_plane(S, gin, -2);
             issue_plane(S, gin, -1);
-            issue_plane(S, gin, 0);
         }
-        pending |= 7u;
-        // prologue: planes -2, -1, 0 -> primitives
+        pending |= 3u;
+        // prologue: planes -2, -1, 0 -> primitives; plane 0 reuses slot 0
         bool timed_out = false;
-        for (int kp = -2; kp <= 0; ++kp) {
-            const int slot = (kp + 2) % 3;
-            if (!timed_out && mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
-                parity ^= 1u << slot;
-                pending &= ~(1u << slot);
-                convert_plane<MODE>(S.raw[slot], S.W[slot], kp, kc, st);
+        if (mbar_wait(&S.mbar[0], parity & 1u)) {
+            parity ^= 1u;
+            pending &= ~1u;
+            convert_plane<MODE>(S.raw[0], S.W[0], -2, kc, st);
+        } else {
+            timed_out = true;
+        }
+        if (__syncthreads_or(timed_out)) goto abort_group;
+        if (tid == 0) issue_plane(S, gin, 0);
+        pending |= 1u;
+        for (int s = 1; s >= 0; --s) {  // plane -1 (slot 1), then plane 0 (slot 0)
+            if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
+                parity ^= 1u << s;
+                pending &= ~(1u << s);
+                convert_plane<MODE>(S.raw[s], S.W[(s == 1) ? 1 : 2], (s == 1) ? -1 : 0, kc, st);
             } else {
                 timed_out = true;
             }
@@ -404,41 +454,36 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
         if (__syncthreads_or(timed_out)) goto abort_group;
 
         {
-            // owner registers
-            T zp0[5], zp1[5], fzo0[5], fzo1[5], D0[5], D1[5], Uo0[5], Uo1[5];
-            double smax = 0.0, ssum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            // owner registers: z+ state of the previous plane, previous z-flux,
+            // U - lam * (x/y flux divergence) of the previous plane
+            T zp0[5], zp1[5], fzo0[5], fzo1[5], E0[5], E1[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                zp0[q] = zp1[q] = fzo0[q] = fzo1[q] = D0[q] = D1[q] = Uo0[q] = Uo1[q] = T(0);
-            }
+            for (int q = 0; q < 5; ++q)
+                zp0[q] = zp1[q] = fzo0[q] = fzo1[q] = E0[q] = E1[q] = T(0);
+            T smax = T(0);
+            SumAcc<T> sums;
 
             for (int k = -1; k <= 16; ++k) {
-                if (k <= 15) {
-                    if (tid == 0) {
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_plane(S, gin, k + 2);
-                    }
-                    pending |= 1u << ((k + 4) % 3);
-                }
                 const T* Wm = S.W[(k + 1) % 3];
                 const T* W0 = S.W[(k + 2) % 3];
                 const T* Wp = S.W[(k + 3) % 3];
-                const T* Uk = S.raw[(k + 2) % 3];
+                const T* Uk = S.raw[(k + 2) & 1];
                 const bool inner = (k >= 0 && k <= 15);
 
                 // ---- phase A: half-step prediction of plane k
-                T zm0[5], zm1[5], zpn0[5], zpn1[5];
+                T zm0[5], zm1[5], zpn0[5], zpn1[5], uc0[5], uc1[5];
                 {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
                     T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, Uk, pc0, half_lam, igm1, kc, fs, st);
+                    predict<MODE>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs, st);
                     if (inner) {
-                        const int p = j0 * 16 + i0;
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
-                            S.xm[q * kFaceStride + p] = fs[0][q];
-                            S.xp[q * kFaceStride + p] = fs[1][q];
-                            S.ym[q * kFaceStride + p] = fs[2][q];
-                            S.yp[q * kFaceStride + p] = fs[3][q];
+                            S.xm[q * kFaceStride + fa0] = fs[0][q];
+                            S.xp[q * kFaceStride + fa0] = fs[1][q];
+                            S.ym[q * kFaceStride + fa0] = fs[2][q];
+                            S.yp[q * kFaceStride + fa0] = fs[3][q];
                         }
                     }
 #pragma unroll
@@ -448,16 +493,17 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                     }
                 }
                 if (two) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc1];
                     T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, Uk, pc1, half_lam, igm1, kc, fs, st);
+                    predict<MODE>(Wm, W0, Wp, uc1, pc1, half_lam, igm1, kc, fs, st);
                     if (inner) {
-                        const int p = j1 * 16 + i0;
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
-                            S.xm[q * kFaceStride + p] = fs[0][q];
-                            S.xp[q * kFaceStride + p] = fs[1][q];
-                            S.ym[q * kFaceStride + p] = fs[2][q];
-                            S.yp[q * kFaceStride + p] = fs[3][q];
+                            S.xm[q * kFaceStride + fa1] = fs[0][q];
+                            S.xp[q * kFaceStride + fa1] = fs[1][q];
+                            S.ym[q * kFaceStride + fa1] = fs[2][q];
+                            S.yp[q * kFaceStride + fa1] = fs[3][q];
                         }
                     }
 #pragma unroll
@@ -465,25 +511,37 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                         zm1[q] = fs[4][q];
                         zpn1[q] = fs[5][q];
                     }
-                } else if (inner) {
-                    T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, Uk, psl, half_lam, igm1, kc, fs, st);
-                    const int p = kFaceStride - 16 + st_;
-                    if (side == 0) {
+                } else {
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) S.xp[q * kFaceStride + p] = fs[1][q];
-                    } else if (side == 1) {
+                    for (int q = 0; q < 5; ++q) zm1[q] = zpn1[q] = uc1[q] = T(0);
+                    if (inner) {
+                        T us[5];
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) S.xm[q * kFaceStride + p] = fs[0][q];
-                    } else if (side == 2) {
+                        for (int q = 0; q < 5; ++q) us[q] = Uk[q * kPlane + psl];
+                        T fs[6][5];
+                        predict<MODE>(Wm, W0, Wp, us, psl, half_lam, igm1, kc, fs, st);
+                        const int p = kFaceStride - 16 + st_;
+                        if (side == 0) {
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) S.yp[q * kFaceStride + p] = fs[3][q];
-                    } else {
+                            for (int q = 0; q < 5; ++q) S.xp[q * kFaceStride + p] = fs[1][q];
+                        } else if (side == 1) {
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) S.ym[q * kFaceStride + p] = fs[2][q];
+                            for (int q = 0; q < 5; ++q) S.xm[q * kFaceStride + p] = fs[0][q];
+                        } else if (side == 2) {
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) S.yp[q * kFaceStride + p] = fs[3][q];
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) S.ym[q * kFaceStride + p] = fs[2][q];
+                        }
                     }
                 }
                 __syncthreads();
+                // plane k has been read: its slot takes plane k+2
+                if (k <= 15) {
+                    if (tid == 0) issue_plane(S, gin, k + 2);
+                    pending |= 1u << ((k + 2) & 1);
+                }
 
                 // ---- phase B: Riemann solves
                 T fz0[5], fz1[5];
@@ -512,6 +570,9 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
 #pragma unroll
                             for (int q = 0; q < 5; ++q) dst[q * 256] = fz1[q];
                         }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) fz1[q] = T(0);
                     }
                 }
                 if (inner) {
@@ -521,20 +582,23 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                     for (int r = 0; r < nxy; ++r) {
                         const int it = two ? (r * 96 + tid) : (288 + r * 64 + (tid - 96));
                         const bool isy = it >= 272;
-                        int lo, hi, a, b;  // left/right state offsets in the face arrays
+                        int lo, hi, wr, a, b;
                         const T *LA, *RA;
                         if (!isy) {
                             const int j = it / 17, f = it - j * 17;
-                            lo = (f == 0) ? (256 + j) : (j * 16 + f - 1);
-                            hi = (f == 16) ? (256 + j) : (j * 16 + f);
+                            const int rj = frow(j) * 16;
+                            lo = (f == 0) ? (256 + j) : (rj + f - 1);
+                            hi = (f == 16) ? (256 + j) : (rj + f);
+                            wr = hi;
                             LA = S.xp;
                             RA = S.xm;
                             a = j;
                             b = f;
                         } else {
                             const int y = it - 272, f = y >> 4, i = y & 15;
-                            lo = (f == 0) ? (256 + i) : ((f - 1) * 16 + i);
-                            hi = (f == 16) ? (256 + i) : (f * 16 + i);
+                            lo = (f == 0) ? (256 + i) : (frow(f - 1) * 16 + i);
+                            hi = (f == 16) ? (256 + i) : (frow(f) * 16 + i);
+                            wr = 272 + hi;
                             LA = S.yp;
                             RA = S.ym;
                             a = i;
@@ -554,11 +618,11 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                         R[3] = RA[c3 * kFaceStride + hi];
                         R[4] = RA[4 * kFaceStride + hi];
                         roe_rot<MODE>(L, R, kc, F, st);
-                        S.fxy[it] = F[0];
-                        S.fxy[c1 * kFluxStride + it] = F[1];
-                        S.fxy[c2 * kFluxStride + it] = F[2];
-                        S.fxy[c3 * kFluxStride + it] = F[3];
-                        S.fxy[4 * kFluxStride + it] = F[4];
+                        S.fxy[wr] = F[0];
+                        S.fxy[c1 * kFluxStride + wr] = F[1];
+                        S.fxy[c2 * kFluxStride + wr] = F[2];
+                        S.fxy[c3 * kFluxStride + wr] = F[3];
+                        S.fxy[4 * kFluxStride + wr] = F[4];
                         if (gff && (b == 0 || b == 16)) {
                             // faces -x,+x: [v][k][j];  -y,+y: [v][k][i]
                             const int face = (isy ? 2 : 0) + (b == 16 ? 1 : 0);
@@ -579,43 +643,47 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (cc == 1 && !two) break;
-                        const T* Uo = cc ? Uo1 : Uo0;
-                        const T* Dd = cc ? D1 : D0;
+                        const T* Ep = cc ? E1 : E0;
                         const T* fo = cc ? fzo1 : fzo0;
                         const T* fn = cc ? fz1 : fz0;
                         const int jj = cc ? j1 : j0;
                         T o[5];
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
-                            o[q] = Uo[q] - lam * (Dd[q] + (fn[q] - fo[q]));
+                            o[q] = Ep[q] - lam * (fn[q] - fo[q]);
                             gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
                         }
-                        // epilogue: positivity flag, FP64 signal speed and sums
+                        // epilogue: positivity flag, signal speed and sums
                         const T ir = rcp_(o[0]);
                         const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
                         if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
                         const T c2 = kc.gamma * p * ir;
                         const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
-                        const T vmax = max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir));
-                        const double sp = static_cast<double>(vmax + cs);
+                        const T sp =
+                            max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
                         if (sp > smax) smax = sp;
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) ssum[q] += static_cast<double>(o[q]);
+                        for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
                     }
                 }
                 if (inner) {
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        const T* fq = S.fxy + q * kFluxStride;
-                        D0[q] = (fq[j0 * 17 + i0 + 1] - fq[j0 * 17 + i0]) +
-                                (fq[272 + (j0 + 1) * 16 + i0] - fq[272 + j0 * 16 + i0]);
-                        Uo0[q] = Uk[q * kPlane + pc0];
-                        fzo0[q] = fz0[q];
-                        if (two) {
-                            D1[q] = (fq[j1 * 17 + i0 + 1] - fq[j1 * 17 + i0]) +
-                                    (fq[272 + (j1 + 1) * 16 + i0] - fq[272 + j1 * 16 + i0]);
-                            Uo1[q] = Uk[q * kPlane + pc1];
-                            fzo1[q] = fz1[q];
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cc == 1 && !two) break;
+                        const int jj = cc ? j1 : j0;
+                        const int fa = cc ? fa1 : fa0;
+                        const int rxp = (i0 == 15) ? (256 + jj) : (fa + 1);
+                        const int ryp = 272 + ((jj == 15) ? (256 + i0) : (frow(jj + 1) * 16 + i0));
+                        const T* uc = cc ? uc1 : uc0;
+                        T* Ec = cc ? E1 : E0;
+                        T* fo = cc ? fzo1 : fzo0;
+                        const T* fn = cc ? fz1 : fz0;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            const T* fq = S.fxy + q * kFluxStride;
+                            const T D = (fq[rxp] - fq[fa]) + (fq[ryp] - fq[272 + fa]);
+                            Ec[q] = uc[q] - lam * D;
+                            fo[q] = fn[q];
                         }
                     }
                 }
@@ -625,11 +693,11 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                     zp1[q] = zpn1[q];
                 }
                 if (k <= 15) {
-                    const int slot = (k + 4) % 3;  // slot of plane k+2
+                    const int slot = (k + 2) & 1;  // slot of plane k+2
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
-                        convert_plane<MODE>(S.raw[slot], S.W[slot], k + 2, kc, st);
+                        convert_plane<MODE>(S.raw[slot], S.W[(k + 4) % 3], k + 2, kc, st);
                     } else {
                         timed_out = true;
                     }
@@ -637,18 +705,22 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
                 if (__syncthreads_or(timed_out)) goto abort_group;
             }
 
-            // ---- group epilogue: reductions
+            // ---- group epilogue: reductions in FP64 across threads
+            double dmax = double(smax);
+            double dsum[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dsum[q] = sums.get(q);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+                dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
 #pragma unroll
-                for (int q = 0; q < 5; ++q) ssum[q] += __shfl_xor_sync(0xffffffffu, ssum[q], off);
+                for (int q = 0; q < 5; ++q) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], off);
             }
             const uint32_t wst = __reduce_or_sync(0xffffffffu, st);
             if (lane == 0) {
-                S.red[warp][0] = smax;
+                S.red[warp][0] = dmax;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) S.red[warp][1 + q] = ssum[q];
+                for (int q = 0; q < 5; ++q) S.red[warp][1 + q] = dsum[q];
                 if (wst) atomicOr(&S.status, wst);
             }
             __syncthreads();
@@ -673,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == GAMER_MODE_F64) ? 1 : 2)
         // still in flight so none lands after the CTA exits, flag the group and
         // stop this CTA.
         if (tid == 0) {
-            for (int s = 0; s < 3; ++s)
+            for (int s = 0; s < 2; ++s)
                 if (pending & (1u << s)) mbar_wait(&S.mbar[s], (parity >> s) & 1u);
             if (status) status[g] = GAMER_ST_INTERNAL_TIMEOUT;
         }

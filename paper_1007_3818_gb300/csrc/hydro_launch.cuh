@@ -40,18 +40,26 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     DeviceInfo dev = current_device();
     if (dev.status != GAMER_OK) return dev.status;
 
-    auto kern = hydro_step_kernel<MODE>;
+    // variant: FP64 has one (1 CTA/SM); FP32 modes are built for 2 and 3 CTAs/SM
+    const int want = hydro_ctas_per_sm_override(MODE);
+    const int minb = (MODE == GAMER_MODE_F64) ? 1 : ((want == 2) ? 2 : 3);
+    void (*kern)(const T*, T*, T*, const double*, const double*, uint32_t*, double*, int64_t,
+                 KConst<T, P>);
+    if constexpr (MODE == GAMER_MODE_F64) {
+        kern = hydro_step_kernel<MODE, 1>;
+    } else {
+        kern = (minb == 2) ? hydro_step_kernel<MODE, 2> : hydro_step_kernel<MODE, 3>;
+    }
     const int smem = int(sizeof(Smem<T>));
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return GAMER_E_CUDA;
-    int per_sm = hydro_ctas_per_sm_override(MODE);
-    if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
-                cudaSuccess ||
-            per_sm < 1)
-            return GAMER_E_CUDA;
-    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return GAMER_E_CUDA;
+    if (want > 0 && want < per_sm) per_sm = want;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
     KConst<T, P> kc;
     kc.gamma = T(p->gamma);
