@@ -143,6 +143,28 @@ int gamer_hydro_dt(const double* partials, int64_t N, const int32_t* level, int3
                    double* dt_group, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gamer_hydro_dt_noalloc: gamer_hydro_dt without a workspace argument, for
+ * callers that cannot allocate device memory -- for example a host AMR code
+ * whose device memory is all owned by its own allocator and that hands this
+ * library only the arrays it already holds, or a binding from a language with
+ * no access to a CUDA allocator.  The paper has no counterpart; this is an
+ * interface convenience.  The scratch is a fixed 64 KiB array in the library's
+ * device memory (held on every GPU that loads the library until the process
+ * exits), so the call allocates nothing.  It accepts the sizes whose workspace,
+ * gamer_hydro_dt_workspace_bytes(N, n_levels), fits in 64 KiB -- every N up to
+ * 64 Ki groups, and every N for n_levels <= 3 -- and returns GAMER_E_WORKSPACE
+ * for larger ones.  Arguments, results and other errors are those of
+ * gamer_hydro_dt.  The first call on a device looks up the scratch array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  All calls share the one array and every call rewrites
+ * the part it reads, so nothing needs clearing between calls; calls whose GPU
+ * work overlaps (different streams, no ordering between them) race on it.
+ */
+int gamer_hydro_dt_noalloc(const double* partials, int64_t N, const int32_t* level,
+                           int32_t n_levels, const double* dh_level, double cfl, double* dt_out,
+                           double* totals, double* dt_group, void* stream);
+
+/*
  * Device-resident uniform-level step as one CUDA graph (ghost fill -> hydro
  * step -> dt reduction, no host round trip).
  * gamer_level_graph_create captures, on a private stream, one step:

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "abi_common.h"
 
@@ -140,4 +141,51 @@ extern "C" int gamer_hydro_dt(const double* partials, int64_t N, const int32_t* 
         dt_scatter<<<unsigned(blocks), kRedThreads, 0, s>>>(dt_out, level, n_levels, N, dt_group);
     }
     return cudaGetLastError() == cudaSuccess ? GAMER_OK : GAMER_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// gamer_hydro_dt_noalloc: gamer_hydro_dt for callers that cannot allocate
+// device memory.  Its scratch is this fixed file-scope device array (64 KiB,
+// present on every GPU that loads the library until the process exits).
+namespace gamer {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+__device__ __align__(256) double g_dt_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+// Device address of g_dt_scratch on the current device, looked up once per
+// device (host code only sees a stand-in for the array, never its address).
+double* noalloc_scratch(int dev) {
+    static std::mutex mu;
+    static double* addr[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dt_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<double*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+}  // namespace gamer
+
+extern "C" int gamer_hydro_dt_noalloc(const double* partials, int64_t N, const int32_t* level,
+                                      int32_t n_levels, const double* dh_level, double cfl,
+                                      double* dt_out, double* totals, double* dt_group,
+                                      void* stream) {
+    using namespace gamer;
+    if (N < 0 || n_levels < 1 || n_levels > kMaxLevels) return GAMER_E_PARAM;
+    const size_t need = gamer_hydro_dt_workspace_bytes(N, n_levels);
+    if (need > kNoAllocScratchBytes) return GAMER_E_WORKSPACE;
+    const DeviceInfo d = current_device();
+    if (d.status != GAMER_OK) return d.status;
+    double* scratch = noalloc_scratch(d.device);
+    if (!scratch) return GAMER_E_CUDA;
+    return gamer_hydro_dt(partials, N, level, n_levels, dh_level, cfl, dt_out, totals, dt_group,
+                          scratch, kNoAllocScratchBytes, stream);
 }

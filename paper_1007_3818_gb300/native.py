@@ -65,6 +65,8 @@ def lib():
         L.gamer_hydro_dt.argtypes = [vp, i64, vp, i32, vp, d, vp, vp, vp, vp, ctypes.c_size_t,
                                      vp]
         L.gamer_hydro_dt.restype = ctypes.c_int
+        L.gamer_hydro_dt_noalloc.argtypes = [vp, i64, vp, i32, vp, d, vp, vp, vp, vp]
+        L.gamer_hydro_dt_noalloc.restype = ctypes.c_int
         L.gamer_strerror.argtypes = [ctypes.c_int]
         L.gamer_strerror.restype = ctypes.c_char_p
         L.gamer_device_check.argtypes = []
@@ -208,6 +210,23 @@ def gamer_hydro_dt(partials, level, dh_level, cfl, dt_out, totals, dt_group, wor
                               _ptr(dt_group, torch.float64, (), "dt_group"),
                               _ptr(workspace, None, None, "workspace"), ws_bytes, _stream(stream))
     _check(rc, "gamer_hydro_dt")
+
+
+def gamer_hydro_dt_noalloc(partials, level, dh_level, cfl, dt_out, totals, dt_group,
+                           stream=None):
+    """gamer_hydro_dt for callers that cannot allocate device memory: the
+    library's fixed 64 KiB device scratch replaces the workspace."""
+    import torch
+    rc = lib().gamer_hydro_dt_noalloc(_ptr(partials, torch.float64, (6,), "partials"),
+                                      int(partials.shape[0]),
+                                      _ptr(level, torch.int32, (), "level"),
+                                      int(dh_level.shape[0]),
+                                      _ptr(dh_level, torch.float64, (), "dh_level"), float(cfl),
+                                      _ptr(dt_out, torch.float64, (), "dt_out"),
+                                      _ptr(totals, torch.float64, (), "totals"),
+                                      _ptr(dt_group, torch.float64, (), "dt_group"),
+                                      _stream(stream))
+    _check(rc, "gamer_hydro_dt_noalloc")
 
 
 def gamer_device_check():
