@@ -59,6 +59,10 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["uniform256", "streamed1024"], default="uniform256",
+                    help="uniform256: device-resident 256^3 level (default); streamed1024: "
+                         "1024^3 level in pinned host memory streamed through the GPU")
+    ap.add_argument("--batch", type=int, default=4096, help="streamed batch size (groups)")
     return ap.parse_args()
 
 
@@ -146,15 +150,19 @@ def cpu_baseline(tiles_f64, seconds):
     t0 = time.perf_counter()
     oracle.advance_groups(probe, dt, dh, gamma=GAMMA, nthreads=cores)
     t_probe = time.perf_counter() - t0
+    # as many groups as the budget allows, repeated steps if the whole level is quicker
     n = int(min(len(tiles_f64), max(cores, cores * round(seconds / max(t_probe, 1e-3)))))
+    reps = max(1, int(round(seconds / max(t_probe * n / cores, 1e-3))))
     sample = tiles_f64[:n]
     t0 = time.perf_counter()
-    oracle.advance_groups(sample, dt, dh, gamma=GAMMA, nthreads=cores)
+    for _ in range(reps):
+        oracle.advance_groups(sample, dt, dh, gamma=GAMMA, nthreads=cores)
     el = time.perf_counter() - t0
     counts = oracle.count_ops_group(tiles_f64[0], dt, dh, gamma=GAMMA)
     flops = (counts["add"] + counts["mul"] + counts["div"] + counts["sqrt"]) / counts["cells"]
-    return n * GROUP_CELLS / el, cores, f"{n} of the {len(tiles_f64)} groups, one step, " \
-        f"{el:.1f} s on {cores} threads (OpenMP over groups)", flops
+    return n * GROUP_CELLS * reps / el, cores, \
+        f"{n} of the {len(tiles_f64)} groups x {reps} step(s), {el:.1f} s on {cores} threads " \
+        f"(OpenMP over groups)", flops
 
 
 def reference_arm(args):
@@ -200,10 +208,69 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------------------
+def streamed_main(args):
+    """1024^3 level (262,144 groups) in pinned host memory; every step the host
+    threads prepare ghost zones batch by batch while the GPU copies in, steps
+    and copies back the previous batches on three streams."""
+    import numpy as np
+    import torch
+    from paper_1007_3818_gb300 import native
+    from paper_1007_3818_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    mode = {"f32": native.GAMER_MODE_F32, "mixed": native.GAMER_MODE_MIXED,
+            "f64": native.GAMER_MODE_F64}[args.mode]
+    T = torch.float64 if mode == native.GAMER_MODE_F64 else torch.float32
+    base = wl.level_to_groups(wl.lognormal_base(256, SEED + 2, gamma=GAMMA,
+                                                sigma_ln=np.log(1e4) / 8, clip=4.0, vel_rms=1.0))
+    gx = 64
+    G = gx ** 3
+    gid = np.arange(G)
+    src = (((gid // (gx * gx)) % 16) * 16 + ((gid // gx) % gx) % 16) * 16 + (gid % gx) % 16
+    lv = [torch.empty((G, 5, 16, 16, 16), dtype=T, pin_memory=True) for _ in range(2)]
+    torch.index_select(torch.from_numpy(base).to(T), 0, torch.from_numpy(src), out=lv[0])
+    part = torch.zeros((G, 6), dtype=torch.float64, pin_memory=True)
+    st = torch.zeros(G, dtype=torch.int32, pin_memory=True)
+    dh = 1.0 / 1024
+    params = native.make_params(GAMMA, cfl=CFL)
+    pl = native.Pipeline(mode, args.batch, with_flux=False)
+    pl.set_timeout(600.0)
+    pl.level_step_host(lv[0], lv[1], gx, gx, gx, 0, 0.0, dh, st, part, params)  # partials of U^0
+    cur = 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt = CFL * dh / float(part[:, 0].max())          # FP64 reduction of the partials
+        pl.level_step_host(lv[cur], lv[1 - cur], gx, gx, gx, 0, dt, dh, st, part, params)
+        cur = 1 - cur
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    pl.close()
+    esz = 8 if T == torch.float64 else 4
+    cells = G * GROUP_CELLS
+    v = cells * args.steps / el
+    print(json.dumps({
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": 1, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.mode, "data": "synthetic",
+        "config": {"workload": "streamed 1024^3 level: 262,144 patch groups in pinned host "
+                               "memory, host ghost fill overlapped with H2D / step / D2H on 3 "
+                               "streams, lognormal density contrast 1e4, gamma 5/3",
+                   "batch_groups": args.batch, "host_threads": os.cpu_count()},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": G * (40000 * esz + 16),
+                "d2h_bytes_per_step": G * (20480 * esz + 52)},
+        "clocks": clk, "status_or": int(np.bitwise_or.reduce(st.numpy())),
+    }), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "streamed1024":
+        return streamed_main(args)
     import numpy as np
     import torch
     from paper_1007_3818_gb300 import dist, native
@@ -248,6 +315,10 @@ def main():
     torch.cuda.synchronize()
     tiles_host0 = tiles.double().cpu().numpy() if (rank == 0 and not args.no_cpu_baseline) else None
     tot0 = totals.cpu().numpy().copy()
+
+    # autotuned launch shape (register/smem variant and CTAs per SM) on this batch
+    from paper_1007_3818_gb300 import tune
+    tuned = tune.tune_hydro(mode, tiles, level_b, ff, dt_g, dh_g, status, partials, params)
 
     cur, nxt = [level_a, level_b], 0
     ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -325,7 +396,8 @@ def main():
         h_dh = dh_g.cpu().pin_memory()
         h_st = torch.empty(G, dtype=torch.int32).pin_memory()
         h_part = torch.empty((G, 6), dtype=torch.float64).pin_memory()
-        pipe = native.Pipeline(mode, 512, with_flux=True)
+        tp = tune.tune_pipeline(mode, h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
+        pipe = native.Pipeline(mode, tp["batch"], with_flux=True)
         for _ in range(2):
             pipe.advance_host(h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
         n_e2e = max(3, min(args.steps, 50))
@@ -340,7 +412,7 @@ def main():
         e2e = {"value": world * cells_per_step * n_e2e / el_e2e, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": n_e2e, "api": "gamer_pipeline_advance_host (pinned host buffers, "
-                                      "3 streams, batches of 512 groups)"}
+                                      "3 streams, batches of %d groups)" % tp["batch"]}
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6702.2)
@@ -380,6 +452,8 @@ def main():
             "e2e": e2e, "clocks": clk,
             "gpu_launches": 5 * args.steps,
             "kernel_ms": {"hydro_step": adv_ms},
+            "tuned": {"ctas_per_sm": tuned["ctas_per_sm"],
+                      "candidates_ms": {str(k): v for k, v in tuned["all"].items()}},
             "graph": {"ms_per_step": el_graph / args.steps * 1e3,
                       "value": world * cells_per_step * args.steps / el_graph},
             "status_or": int(np.bitwise_or.reduce(st)),

@@ -214,6 +214,34 @@ int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_host, void* o
                                 const double* dh_host, uint32_t* status_host,
                                 double* partials_host, int64_t N, const gh_params* p);
 int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds);
+
+/*
+ * gamer_pipeline_level_step_host: one step of a uniform level that lives in
+ * HOST memory (the paper's arrangement: the CPU prepares ghost zones while the
+ * GPU solves, Sec. 2).  For each batch of the pipeline's size, host threads
+ * (nthreads, <= 0: all) build the ghost-padded tiles from level_in_host into a
+ * pinned staging buffer while the GPU copies, advances and copies back the
+ * batches queued before it; results go straight into level_out_host.
+ * level_in_host, level_out_host [G][5][16]^3 (G = gx*gy*gz, element type by
+ * mode, distinct, ideally pinned); bc 0 periodic, 1 zero-gradient; one dt, dh
+ * for the level; status_host [G] and partials_host [G][6] may be NULL.  The
+ * first call allocates three pinned staging buffers of the batch size (held
+ * until gamer_pipeline_destroy); later calls allocate nothing.  Bounded waits
+ * as for gamer_pipeline_advance_host; no face fluxes.
+ */
+int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* level_in_host,
+                                   void* level_out_host, int32_t gx, int32_t gy, int32_t gz,
+                                   int32_t bc, double dt, double dh, uint32_t* status_host,
+                                   double* partials_host, const gh_params* p, int32_t nthreads);
+
+/*
+ * gamer_fill_ghosts_uniform_host_{f32,f64}: gamer_fill_ghosts_uniform_* on
+ * HOST arrays, run by nthreads CPU threads (<= 0: all).  Synchronous.
+ */
+int gamer_fill_ghosts_uniform_host_f32(const float* level, float* in, int32_t gx, int32_t gy,
+                                       int32_t gz, int32_t bc, int32_t nthreads);
+int gamer_fill_ghosts_uniform_host_f64(const double* level, double* in, int32_t gx, int32_t gy,
+                                       int32_t gz, int32_t bc, int32_t nthreads);
 int gamer_pipeline_destroy(gamer_pipeline* pl);
 
 /* Message for a GAMER_E* return code (static string). */

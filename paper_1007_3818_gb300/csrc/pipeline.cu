@@ -40,6 +40,10 @@ struct BufSet {
 }  // namespace
 
 struct gamer_pipeline {
+    // pinned host staging of ghost-padded tiles for level steps (allocated on
+    // the first gamer_pipeline_level_step_host call)
+    void* staging[3] = {nullptr, nullptr, nullptr};
+    double* stage_dt = nullptr;  // pinned [2][batch]: dt, dh of a level step
     int mode = 0;
     int64_t batch = 0;
     int with_flux = 0;
@@ -54,6 +58,9 @@ namespace {
 
 void release(gamer_pipeline* pl) {
     if (!pl) return;
+    for (auto& st : pl->staging)
+        if (st) cudaFreeHost(st);
+    if (pl->stage_dt) cudaFreeHost(pl->stage_dt);
     for (auto& b : pl->set) {
         cudaFree(b.in);
         cudaFree(b.out);
@@ -204,6 +211,105 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     // results are in host memory when the last device->host copies are done
     const BufSet& last = pl->set[(nb - 1) % kSets];
     return wait_event(last.d2h_done, pl->timeout_s);
+}
+
+namespace gamer {
+template <class T>
+void fill_tiles_host(const T* level, T* out, int gx, int gy, int gz, int bc, int64_t g0,
+                     int64_t g1, int nthreads);
+}
+
+extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* level_in_host,
+                                              void* level_out_host, int32_t gx, int32_t gy,
+                                              int32_t gz, int32_t bc, double dt, double dh,
+                                              uint32_t* status_host, double* partials_host,
+                                              const gh_params* p, int32_t nthreads) {
+    using namespace gamer;
+    if (!pl) return GAMER_E_NULL;
+    int rc = check_params(p);
+    if (rc != GAMER_OK) return rc;
+    if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1)) return GAMER_E_PARAM;
+    const int64_t G = int64_t(gx) * gy * gz;
+    if (G == 0) return GAMER_OK;
+    if (!level_in_host || !level_out_host) return GAMER_E_NULL;
+    if (level_in_host == level_out_host) return GAMER_E_OVERLAP;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return GAMER_E_DEVICE;
+    const size_t e = pl->esz;
+    const size_t tile_bytes = size_t(pl->batch) * 40000 * e;
+    if (!pl->staging[0]) {
+        for (auto& st : pl->staging)
+            if (cudaHostAlloc(&st, tile_bytes, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                return GAMER_E_CUDA;
+            }
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pl->stage_dt), size_t(pl->batch) * 16,
+                          cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return GAMER_E_CUDA;
+        }
+    }
+    // every group of the level takes the same dt and dh
+    for (int64_t i = 0; i < pl->batch; ++i) {
+        pl->stage_dt[i] = dt;
+        pl->stage_dt[pl->batch + i] = dh;
+    }
+    const double* hdt = pl->stage_dt;
+    const double* hdh = pl->stage_dt + pl->batch;
+    char* hout = static_cast<char*>(level_out_host);
+    const int64_t nb = (G + pl->batch - 1) / pl->batch;
+    for (int64_t b = 0; b < nb; ++b) {
+        BufSet& S = pl->set[b % kSets];
+        char* stg = static_cast<char*>(pl->staging[b % kSets]);
+        const int64_t g0 = b * pl->batch;
+        const int64_t n = std::min<int64_t>(pl->batch, G - g0);
+        // the staging buffer is refilled only once its previous copy has left
+        if (S.used && (rc = wait_event(S.h2d_done, pl->timeout_s)) != GAMER_OK) return rc;
+        // host ghost preparation of this batch overlaps the GPU work queued before it
+        if (pl->mode == GAMER_MODE_F64)
+            fill_tiles_host<double>(static_cast<const double*>(level_in_host),
+                                    reinterpret_cast<double*>(stg), gx, gy, gz, bc, g0, g0 + n,
+                                    nthreads);
+        else
+            fill_tiles_host<float>(static_cast<const float*>(level_in_host),
+                                   reinterpret_cast<float*>(stg), gx, gy, gz, bc, g0, g0 + n,
+                                   nthreads);
+        if (S.used && cudaStreamWaitEvent(pl->s_h2d, S.d2h_done, 0) != cudaSuccess)
+            return GAMER_E_CUDA;
+        bool ok = cudaMemcpyAsync(S.in, stg, size_t(n) * 40000 * e, cudaMemcpyHostToDevice,
+                                  pl->s_h2d) == cudaSuccess &&
+                  cudaMemcpyAsync(S.dt, hdt, size_t(n) * 8, cudaMemcpyHostToDevice,
+                                  pl->s_h2d) == cudaSuccess &&
+                  cudaMemcpyAsync(S.dh, hdh, size_t(n) * 8, cudaMemcpyHostToDevice,
+                                  pl->s_h2d) == cudaSuccess &&
+                  cudaEventRecord(S.h2d_done, pl->s_h2d) == cudaSuccess &&
+                  cudaStreamWaitEvent(pl->s_comp, S.h2d_done, 0) == cudaSuccess;
+        if (!ok) return GAMER_E_CUDA;
+        if (pl->mode == GAMER_MODE_F32)
+            rc = gamer_hydro_advance_f32((const float*)S.in, (float*)S.out, nullptr, S.dt, S.dh,
+                                         S.status, S.partials, n, p, pl->s_comp);
+        else if (pl->mode == GAMER_MODE_MIXED)
+            rc = gamer_hydro_advance_mixed((const float*)S.in, (float*)S.out, nullptr, S.dt,
+                                           S.dh, S.status, S.partials, n, p, pl->s_comp);
+        else
+            rc = gamer_hydro_advance_f64((const double*)S.in, (double*)S.out, nullptr, S.dt,
+                                         S.dh, S.status, S.partials, n, p, pl->s_comp);
+        if (rc != GAMER_OK) return rc;
+        ok = cudaEventRecord(S.comp_done, pl->s_comp) == cudaSuccess &&
+             cudaStreamWaitEvent(pl->s_d2h, S.comp_done, 0) == cudaSuccess &&
+             cudaMemcpyAsync(hout + size_t(g0) * 20480 * e, S.out, size_t(n) * 20480 * e,
+                             cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+        if (ok && status_host)
+            ok = cudaMemcpyAsync(status_host + g0, S.status, size_t(n) * 4,
+                                 cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+        if (ok && partials_host)
+            ok = cudaMemcpyAsync(partials_host + g0 * 6, S.partials, size_t(n) * 48,
+                                 cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+        ok = ok && cudaEventRecord(S.d2h_done, pl->s_d2h) == cudaSuccess;
+        if (!ok) return GAMER_E_CUDA;
+        S.used = true;
+    }
+    return wait_event(pl->set[(nb - 1) % kSets].d2h_done, pl->timeout_s);
 }
 
 extern "C" int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds) {

@@ -92,6 +92,13 @@ def lib():
         L.gamer_pipeline_advance_host.restype = ctypes.c_int
         L.gamer_pipeline_set_timeout.argtypes = [vp, d]
         L.gamer_pipeline_set_timeout.restype = ctypes.c_int
+        L.gamer_pipeline_level_step_host.argtypes = [vp, vp, vp, i32, i32, i32, i32, d, d, vp, vp,
+                                                     P(gh_params), i32]
+        L.gamer_pipeline_level_step_host.restype = ctypes.c_int
+        for name in ("gamer_fill_ghosts_uniform_host_f32", "gamer_fill_ghosts_uniform_host_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, i32, i32, i32, i32, i32]
+            f.restype = ctypes.c_int
         L.gamer_pipeline_destroy.argtypes = [vp]
         L.gamer_pipeline_destroy.restype = ctypes.c_int
         _lib = L
@@ -317,6 +324,19 @@ class Pipeline:
                                                ctypes.byref(params))
         _check(rc, "gamer_pipeline_advance_host")
 
+    def level_step_host(self, level_in, level_out, gx, gy, gz, bc, dt, dh, status, partials,
+                        params, nthreads=0):
+        """One step of a host-resident uniform level (host tensors [G,5,16,16,16])."""
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        for t, nm in ((level_in, "level_in"), (level_out, "level_out")):
+            if t.is_cuda or not t.is_contiguous():
+                raise GamerError(-2, f"{nm} must be a contiguous host tensor")
+        rc = lib().gamer_pipeline_level_step_host(self.handle, p(level_in), p(level_out), gx, gy,
+                                                  gz, bc, float(dt), float(dh), p(status),
+                                                  p(partials), ctypes.byref(params),
+                                                  int(nthreads))
+        _check(rc, "gamer_pipeline_level_step_host")
+
     def close(self):
         if self.handle:
             lib().gamer_pipeline_destroy(self.handle)
@@ -327,3 +347,20 @@ class Pipeline:
             self.close()
         except Exception:
             pass
+
+
+def gamer_fill_ghosts_uniform_host(level, inp, gx, gy, gz, bc, nthreads=0):
+    """Host-array ghost fill (CPU threads); level/inp contiguous CPU tensors or
+    numpy arrays of float32 / float64."""
+    import numpy as np
+    lv = level.numpy() if hasattr(level, "numpy") else level
+    out = inp.numpy() if hasattr(inp, "numpy") else inp
+    if lv.dtype != out.dtype or lv.dtype not in (np.float32, np.float64):
+        raise GamerError(-2, "level and in must share a float32 / float64 dtype")
+    if not (lv.flags.c_contiguous and out.flags.c_contiguous):
+        raise GamerError(-2, "level and in must be contiguous")
+    name = ("gamer_fill_ghosts_uniform_host_f32" if lv.dtype == np.float32
+            else "gamer_fill_ghosts_uniform_host_f64")
+    rc = getattr(lib(), name)(ctypes.c_void_p(lv.ctypes.data), ctypes.c_void_p(out.ctypes.data),
+                              gx, gy, gz, bc, int(nthreads))
+    _check(rc, name)

@@ -1,0 +1,107 @@
+"""Autotuner for the launch shape of the hydro step and the host pipeline.
+
+The hydro kernel's work decomposition fixes 160 threads per patch group (320
+predictions and 800 Riemann solves per plane divide evenly); what is left to
+choose per GPU and precision mode is the register / shared-memory split and
+the persistent grid:
+
+  * variant: the build sized for 2 CTAs per SM (no register spills) or for 3
+    (more warps per SM, a few spills);
+  * CTAs per SM actually launched (1 .. the variant's limit);
+  * for the streamed host pipeline, the batch size in groups.
+
+Each candidate is timed with CUDA events on a batch of the caller's shape and
+the fastest is applied through ``gamer_set_hydro_ctas_per_sm``.  Results are
+cached per (GPU name, mode, N bucket) in memory and, if a path is given, in a
+JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+from . import native
+
+_cache = {}
+
+
+def _bucket(n):
+    b = 1
+    while b < n:
+        b *= 2
+    return b
+
+
+def _time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tune_hydro(mode, inp, out, face_flux, dt, dh, status, partials, params, reps=5,
+               cache_path=None):
+    """Time every launch shape of gamer_hydro_advance_<mode> on the given
+    device tensors, apply the fastest and return {"ctas_per_sm", "ms", "all"}."""
+    import torch
+    key = (torch.cuda.get_device_name(), int(mode), _bucket(int(inp.shape[0])))
+    if key in _cache:
+        native.gamer_set_hydro_ctas_per_sm(mode, _cache[key]["ctas_per_sm"])
+        return _cache[key]
+    candidates = [1] if mode == native.GAMER_MODE_F64 else [1, 2, 3]
+    results = {}
+    for c in candidates:
+        native.gamer_set_hydro_ctas_per_sm(mode, c)
+        results[c] = _time(lambda: native.hydro_advance(mode, inp, out, face_flux, dt, dh, status,
+                                                        partials, params), reps)
+    best = min(results, key=results.get)
+    native.gamer_set_hydro_ctas_per_sm(mode, best)
+    res = {"ctas_per_sm": best, "ms": results[best], "all": results}
+    _cache[key] = res
+    if cache_path:
+        _save(cache_path, key, res)
+    return res
+
+
+def tune_pipeline(mode, h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params,
+                  batches=(256, 512, 1024), reps=3):
+    """Pick the pipeline batch size (groups) for host buffers of this shape."""
+    import time
+    results = {}
+    for b in batches:
+        pl = native.Pipeline(mode, b, with_flux=h_ff is not None)
+        pl.advance_host(h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            pl.advance_host(h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
+            ts.append(time.perf_counter() - t0)
+        pl.close()
+        results[b] = statistics.median(ts) * 1e3
+    best = min(results, key=results.get)
+    return {"batch": best, "ms": results[best], "all": results}
+
+
+def _save(path, key, res):
+    data = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+    data["|".join(map(str, key))] = res
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, default=str)
+    os.replace(tmp, path)

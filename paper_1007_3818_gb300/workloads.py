@@ -258,3 +258,34 @@ def stress_groups(N, seed=DEFAULT_SEED, gamma=1.4):
         U = to_conserved(rho, u, v, w, p, gamma)
         out[t] = U[:, idx[:, None, None], idx[None, :, None], idx[None, None, :]]
     return out
+
+
+def window_tiles_torch(base, origins, device):
+    """window_tiles on a torch device: the same periodic 20^3 windows by pure
+    indexing (bit-identical values).  base: numpy [5][n][n][n]; origins [N][3]
+    (x, y, z).  Returns a float64 tensor [N][5][20][20][20] on `device`."""
+    import torch
+    n = base.shape[1]
+    b = torch.as_tensor(np.ascontiguousarray(base), device=device)
+    o = torch.as_tensor(np.asarray(origins), device=device, dtype=torch.int64)
+    off = torch.arange(20, device=device)
+    ix = (o[:, 0:1] + off) % n
+    iy = (o[:, 1:2] + off) % n
+    iz = (o[:, 2:3] + off) % n
+    flat = b.reshape(5, -1)
+    lin = (iz[:, :, None, None] * n + iy[:, None, :, None]) * n + ix[:, None, None, :]
+    return flat[:, lin.reshape(-1)].reshape(5, len(o), 20, 20, 20).transpose(0, 1).contiguous()
+
+
+def amr_batch_parts(counts=(2000, 12000, 40000), seed=DEFAULT_SEED, gamma=5.0 / 3.0, base_n=128,
+                    dh0=1.0 / 256.0, sigma_ln=1.5):
+    """The pieces amr_batch draws (base field, origins, level, dh per level),
+    for generating the full batch on a device with window_tiles_torch."""
+    rng = np.random.default_rng(seed)
+    base = lognormal_base(base_n, seed + 1, gamma=gamma, sigma_ln=sigma_ln, vel_rms=1.0)
+    level = np.concatenate([np.full(c, l, dtype=np.int32) for l, c in enumerate(counts)])
+    perm = rng.permutation(level.shape[0])
+    level = level[perm]
+    origins = rng.integers(0, base_n, size=(level.shape[0], 3))
+    dh_level = np.array([dh0 / (2 ** l) for l in range(len(counts))])
+    return base, origins, level, dh_level

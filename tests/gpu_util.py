@@ -45,21 +45,29 @@ def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, wit
 
 
 def rel_l1_fields(a, b):
-    """max over fields v of sum|a-b| / sum|b| (axis 1 = field).  A field that is
+    """Relative L1 error, max over the conserved fields (axis 1):
+    density and energy sum|a-b| / sum|b|; each momentum component
+    sum|a-b| / sum|m_b|, with |m_b| the momentum magnitude per cell (so the
+    measure does not depend on the orientation of the flow and a component
+    that happens to be tiny is not judged against itself).  A field that is
     identically zero in b must be exactly zero in a (else inf)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
+    if not np.isfinite(a).all():
+        return float("inf")
     worst = 0.0
-    for v in range(a.shape[1]):
+    nf = a.shape[1]
+    mag = None
+    if nf == 5:
+        mag = np.abs(np.sqrt(b[:, 1] ** 2 + b[:, 2] ** 2 + b[:, 3] ** 2)).sum()
+    for v in range(nf):
         av, bv = a[:, v], b[:, v]
-        den = np.abs(bv).sum()
         num = np.abs(av - bv).sum()
-        if den == 0.0:
-            if num != 0.0 or not np.isfinite(av).all():
+        if not np.abs(bv).any():
+            if num != 0.0:
                 return float("inf")
             continue
-        if not np.isfinite(num):
-            return float("inf")
+        den = mag if (mag is not None and 1 <= v <= 3) else np.abs(bv).sum()
         worst = max(worst, num / den)
     return worst
 

@@ -1,0 +1,218 @@
+"""Full-size workloads on the GPU against the oracle.
+
+* uniform periodic 256^3 level (4096 groups): one step through the CUDA-graph
+  launch that the benchmark times (ghost fill -> hydro step -> dt reduction),
+  every group compared with the oracle, plus the next dt and the totals;
+* Sedov blast and Kelvin-Helmholtz 256^3 boxes, every group, one step;
+* the AMR-shaped batch of 54,000 independent tiles on 3 levels, per-level dt
+  from the device reduction, sampled groups compared.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_F32_1, TOL_F64, rel_l1_fields
+from paper_1007_3818_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+F32, MIXED, F64 = 0, 1, 2
+CORES = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def fourier_level():
+    return wl.level_to_groups(wl.fourier_level(n=256, seed=1007, gamma=5 / 3))
+
+
+def _graph_step(level_groups, mode, gamma, dt, dh, gx=16):
+    """One device-resident level step through gamer_level_graph (bench path)."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    T = torch.float64 if mode == F64 else torch.float32
+    G = gx ** 3
+    a = torch.from_numpy(level_groups).to("cuda", T)
+    b = torch.empty_like(a)
+    tiles = torch.empty((G, 5, 20, 20, 20), device="cuda", dtype=T)
+    ff = torch.empty((G, 6, 5, 16, 16), device="cuda", dtype=T)
+    dt_g = torch.full((G,), dt, device="cuda", dtype=torch.float64)
+    dh_g = torch.full((G,), dh, device="cuda", dtype=torch.float64)
+    st = torch.zeros(G, device="cuda", dtype=torch.int32)
+    part = torch.zeros((G, 6), device="cuda", dtype=torch.float64)
+    dh_level = torch.tensor([dh], device="cuda", dtype=torch.float64)
+    dt_level = torch.zeros(1, device="cuda", dtype=torch.float64)
+    tot = torch.zeros(5, device="cuda", dtype=torch.float64)
+    ws = torch.empty(native.gamer_hydro_dt_workspace_bytes(G, 1), device="cuda", dtype=torch.uint8)
+    params = native.make_params(gamma, cfl=0.5)
+    g = native.LevelGraph(mode, a, b, tiles, ff, dt_g, dh_g, st, part, gx, gx, gx, 0, params,
+                          dh_level, dt_level, tot, ws)
+    g.launch()
+    torch.cuda.synchronize()
+    g.close()
+    return (b.double().cpu().numpy(), ff.double().cpu().numpy(), st.cpu().numpy(),
+            part.cpu().numpy(), float(dt_level.item()), tot.cpu().numpy(), dt_g.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode,tol", [(F32, TOL_F32_1), (MIXED, TOL_F32_1), (F64, TOL_F64)],
+                         ids=["f32", "mixed", "f64"])
+def test_uniform_level_full_size_graph_step(fourier_level, mode, tol):
+    g, dh = 5 / 3, 1 / 256
+    lv = fourier_level if mode == F64 else fourier_level.astype(np.float32).astype(np.float64)
+    tiles = oracle.fill_ghosts_uniform(lv, 16, 16, 16, 0)
+    _, _, _, p0 = oracle.advance_groups(tiles, 0.0, dh, gamma=g, nthreads=CORES, want_flux=False)
+    dt = oracle.hydro_dt(p0, [dh], 0.5)[0][0]
+    r_out, r_ff, r_st, r_part = oracle.advance_groups(tiles, dt, dh, gamma=g, nthreads=CORES)
+    out, ff, st, part, dt_next, tot, dt_g = _graph_step(lv, mode, g, dt, dh)
+    assert rel_l1_fields(out, r_out) <= tol
+    assert rel_l1_fields(ff.reshape(-1, 5, 256), r_ff.reshape(-1, 5, 256)) <= 10 * tol
+    assert np.array_equal(st.astype(np.uint32), r_st)
+    r_dt, r_tot = oracle.hydro_dt(r_part, [dh], 0.5)
+    ptol = 1e-12 if mode == F64 else 10 * tol
+    assert abs(dt_next - r_dt[0]) <= ptol * r_dt[0]
+    assert np.all(np.abs(tot - r_tot) <= ptol * np.abs(r_out).reshape(-1, 5, 4096).sum(axis=(0, 2)))
+    assert (dt_g == dt_next).all()
+
+
+def _box_tiles(U):
+    return oracle.fill_ghosts_uniform(wl.level_to_groups(U), U.shape[3] // 16, U.shape[2] // 16,
+                                      U.shape[1] // 16, 0)
+
+
+@pytest.mark.parametrize("problem", ["sedov", "kh"])
+@pytest.mark.parametrize("mode", [F32, MIXED, F64], ids=["f32", "mixed", "f64"])
+def test_sedov_and_kh_full_size_one_step(problem, mode):
+    """Config 3 boxes (256^3 each), every group, one CFL-0.5 step.  FP64 holds
+    1e-12; the FP32 modes are bounded by 1e-5 on KH (smooth away from the
+    layers) and report the Sedov error, where the FP32 storage of E alone
+    carries the cancellation (rho v^2 / 2 >> p)."""
+    from gpu_util import gpu_advance, host_input
+    g, dh = 5 / 3, 1 / 256
+    U = wl.sedov_level(256, gamma=g) if problem == "sedov" else wl.kh_level(256, gamma=g)
+    tiles = host_input(_box_tiles(U), mode)
+    _, _, _, p0 = oracle.advance_groups(tiles, 0.0, dh, gamma=g, nthreads=CORES, want_flux=False)
+    dt = oracle.hydro_dt(p0, [dh], 0.5)[0][0]
+    r_out, _, r_st, _ = oracle.advance_groups(tiles, dt, dh, gamma=g, nthreads=CORES,
+                                              want_flux=False)
+    out, _, st, _ = gpu_advance(tiles, dt, dh, g, mode, with_flux=False)
+    err = rel_l1_fields(out, r_out)
+    print(f"{problem} mode {mode}: rel-L1 {err:.3e}")
+    if mode == F64:
+        assert err <= TOL_F64
+        assert np.array_equal(st, r_st)
+    elif problem == "kh":
+        assert err <= TOL_F32_1
+    else:
+        assert err <= 1e-4
+
+
+@pytest.mark.parametrize("mode,tol", [(F32, TOL_F32_1), (F64, TOL_F64)], ids=["f32", "f64"])
+def test_amr_batch_full_size_sampled(mode, tol):
+    """Config 4: 2,000 / 12,000 / 40,000 tiles at dh 1/256, 1/512, 1/1024,
+    shuffled; dt per level from the device FP64 reduction of a zero-length
+    step; one step of all 54,000 tiles in one launch, 48 sampled tiles checked."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    base, origins, level, dh_level = wl.amr_batch_parts()
+    N = len(level)
+    T = torch.float64 if mode == F64 else torch.float32
+    tiles = wl.window_tiles_torch(base, origins, "cuda").to(T)
+    d_level = torch.as_tensor(level, device="cuda")
+    d_dhl = torch.as_tensor(dh_level, device="cuda")
+    d_dh = d_dhl[d_level.long()].contiguous()
+    d_dt = torch.zeros(N, device="cuda", dtype=torch.float64)
+    out = torch.empty((N, 5, 16, 16, 16), device="cuda", dtype=T)
+    part = torch.empty((N, 6), device="cuda", dtype=torch.float64)
+    st = torch.zeros(N, device="cuda", dtype=torch.int32)
+    params = native.make_params(g)
+    native.hydro_advance(mode, tiles, out, None, d_dt, d_dh, None, part, params)
+    dt_level = torch.zeros(3, device="cuda", dtype=torch.float64)
+    ws = torch.empty(native.gamer_hydro_dt_workspace_bytes(N, 3), device="cuda", dtype=torch.uint8)
+    native.gamer_hydro_dt(part, d_level, d_dhl, 0.5, dt_level, None, d_dt, ws)
+    native.hydro_advance(mode, tiles, out, None, d_dt, d_dh, st, part, params)
+    torch.cuda.synchronize()
+    sample = np.unique(np.r_[0, N - 1, np.random.default_rng(5).integers(0, N, 46)])
+    host = wl.window_tiles(base, origins[sample])
+    if mode != F64:
+        host = host.astype(np.float32).astype(np.float64)
+    dts = d_dt.cpu().numpy()[sample]
+    r_out, _, r_st, r_part = oracle.advance_groups(host, dts, dh_level[level[sample]], gamma=g,
+                                                   nthreads=CORES, want_flux=False)
+    assert rel_l1_fields(out.double().cpu().numpy()[sample], r_out) <= tol
+    assert np.array_equal(st.cpu().numpy()[sample].astype(np.uint32), r_st)
+    # the per-level dt are CFL-limited by each level's own groups
+    assert (dt_level.cpu().numpy() > 0).all()
+
+
+@pytest.mark.parametrize("mode,tol", [(F32, TOL_F32_1), (F64, TOL_F64)], ids=["f32", "f64"])
+def test_pipeline_level_step_small(mode, tol):
+    """Host-resident level through the streamed pipeline (host ghost fill +
+    H2D / step / D2H overlap), batches that do not divide the level."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g, dh, dt = 5 / 3, 1 / 64, 1.5e-3
+    lv = wl.level_to_groups(wl.fourier_level(n=64, seed=3, gamma=g))
+    T = torch.float64 if mode == F64 else torch.float32
+    if mode != F64:
+        lv = lv.astype(np.float32).astype(np.float64)
+    h_in = torch.from_numpy(lv).to(T).pin_memory()
+    h_out = torch.full_like(h_in, float("nan")).pin_memory()
+    part = torch.zeros((64, 6), dtype=torch.float64).pin_memory()
+    st = torch.zeros(64, dtype=torch.int32).pin_memory()
+    pl = native.Pipeline(mode, 24, with_flux=False)
+    pl.level_step_host(h_in, h_out, 4, 4, 4, 0, dt, dh, st, part, native.make_params(g))
+    pl.close()
+    tiles = oracle.fill_ghosts_uniform(lv, 4, 4, 4, 0)
+    r_out, _, r_st, r_part = oracle.advance_groups(tiles, dt, dh, gamma=g, want_flux=False)
+    assert rel_l1_fields(h_out.double().numpy(), r_out) <= tol
+    assert np.array_equal(st.numpy().astype(np.uint32), r_st)
+
+
+def test_streamed_level_full_size_sampled():
+    """Config 5: a 1024^3 level (64^3 = 262,144 groups, 42 GB of FP32 tiles
+    per step) held in pinned host memory, one streamed step (host ghost fill
+    overlapped with H2D / step / D2H on 3 streams); 24 sampled groups checked.
+    The level tiles a periodic 256^3 lognormal field of density contrast 1e4,
+    so each group's ghost-padded input is that of a group of the 256^3 field."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    base = wl.level_to_groups(wl.lognormal_base(256, 1007 + 2, gamma=g, sigma_ln=np.log(1e4) / 8,
+                                                clip=4.0, vel_rms=1.0)).astype(np.float32)
+    gx = 64
+    G = gx ** 3
+    gid = np.arange(G)
+    bx, by, bz = gid % gx, (gid // gx) % gx, gid // (gx * gx)
+    src = ((bz % 16) * 16 + (by % 16)) * 16 + (bx % 16)
+    h_in = torch.empty((G, 5, 16, 16, 16), dtype=torch.float32, pin_memory=True)
+    torch.index_select(torch.from_numpy(base), 0, torch.from_numpy(src), out=h_in)
+    h_out = torch.empty_like(h_in, pin_memory=True)
+    part = torch.zeros((G, 6), dtype=torch.float64, pin_memory=True)
+    st = torch.zeros(G, dtype=torch.int32, pin_memory=True)
+    base64 = base.astype(np.float64)
+    tiles = oracle.fill_ghosts_uniform(base64, 16, 16, 16, 0)
+    dh = 1.0 / 1024
+    _, _, _, p0 = oracle.advance_groups(tiles, 0.0, dh, gamma=g, nthreads=CORES, want_flux=False)
+    dt = oracle.hydro_dt(p0, [dh], 0.5)[0][0]
+    pl = native.Pipeline(F32, 4096, with_flux=False)
+    pl.level_step_host(h_in, h_out, gx, gx, gx, 0, dt, dh, st, part, native.make_params(g))
+    pl.close()
+    sample = np.unique(np.r_[0, G - 1, np.random.default_rng(9).integers(0, G, 22)])
+    r_out, _, r_st, _ = oracle.advance_groups(tiles[src[sample]], dt, dh, gamma=g,
+                                              nthreads=CORES, want_flux=False)
+    got = h_out[torch.from_numpy(sample)].double().numpy()
+    assert rel_l1_fields(got, r_out) <= TOL_F32_1
+    assert np.array_equal(st.numpy()[sample].astype(np.uint32), r_st)
