@@ -452,8 +452,8 @@ def main():
             "e2e": e2e, "clocks": clk,
             "gpu_launches": 5 * args.steps,
             "kernel_ms": {"hydro_step": adv_ms},
-            "tuned": {"ctas_per_sm": tuned["ctas_per_sm"],
-                      "candidates_ms": {str(k): v for k, v in tuned["all"].items()}},
+            "tuned": {"ctas_per_sm": tuned["ctas_per_sm"], "variant": tuned["variant"],
+                      "candidates_ms": tuned["all"]},
             "graph": {"ms_per_step": el_graph / args.steps * 1e3,
                       "value": world * cells_per_step * args.steps / el_graph},
             "status_or": int(np.bitwise_or.reduce(st)),

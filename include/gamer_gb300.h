@@ -262,6 +262,11 @@ const char* gamer_version(void);
  * process-wide setting. */
 int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
 
+/* Code shape of the FP32 hydro kernel's 3-CTA build: 0 = Riemann solver
+ * inlined at each call site (default), 1 = one out-of-line copy (smaller code,
+ * a call per solve).  Used by the autotuner; process-wide setting. */
+int gamer_set_hydro_variant(int32_t variant);
+
 /* Throughput probes for the roofline denominators (not part of the scheme).
  * kind 0: FP32 FMA, 1: FP64 FMA, 2: FP32 MUFU reciprocal -- a grid of
  * 8 x 256 threads per SM, 8 dependent chains of `iters` operations per thread;

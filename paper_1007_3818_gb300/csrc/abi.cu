@@ -34,6 +34,11 @@ DeviceInfo current_device() {
     return d;
 }
 
+int& hydro_variant() {
+    static int v = 0;
+    return v;
+}
+
 int& hydro_ctas_per_sm_override(int mode) {
     static int v[3] = {0, 0, 0};
     return v[(mode >= 0 && mode < 3) ? mode : 0];
@@ -65,5 +70,11 @@ extern "C" const char* gamer_version(void) {
 extern "C" int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm) {
     if (mode < 0 || mode > 2 || ctas_per_sm < 0 || ctas_per_sm > 16) return GAMER_E_PARAM;
     gamer::hydro_ctas_per_sm_override(mode) = ctas_per_sm;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_set_hydro_variant(int32_t variant) {
+    if (variant < 0 || variant > 1) return GAMER_E_PARAM;
+    gamer::hydro_variant() = variant;
     return GAMER_OK;
 }

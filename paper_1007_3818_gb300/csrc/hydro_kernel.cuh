@@ -40,7 +40,7 @@ namespace gamer {
 
 constexpr int kThreads = 160;
 constexpr int kPlane = 400;       // 20 x 20 cells per input plane
-constexpr int kFaceStride = 272;  // 16^2 interior + 16 slab entries per face array
+constexpr int kFaceStride = 288;  // 16^2 interior, 16 slab entries, 16 write-only entries
 constexpr int kFluxStride = 544;  // 16 x 17 x-faces + 17 x 16 y-faces
 
 template <int MODE> struct Prec;
@@ -215,6 +215,49 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
     F[4] = T(0.5) * (FL[4] + FR[4]) - T(0.5) * D4;
 }
 
+// Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
+// states and flux travel by value, the status bits come back in the result.
+template <class T>
+struct RoeIO {
+    T v[5];
+    uint32_t st;
+};
+template <int MODE, class T, class P>
+__device__ __noinline__ RoeIO<T> roe_call(RoeIO<T> L, RoeIO<T> R, KConst<T, P> kc) {
+    RoeIO<T> out;
+    out.st = 0;
+    roe_rot<MODE>(L.v, R.v, kc, out.v, out.st);
+    return out;
+}
+
+// Riemann solve through the inline or the out-of-line solver (OOL = 1).
+template <int OOL> struct RoeTag {};
+template <int MODE, class T, class P>
+__device__ __forceinline__ void roe_pick(RoeTag<0>, const T L[5], const T R[5],
+                                         const KConst<T, P>& kc, T F[5], uint32_t& st) {
+    roe_rot<MODE>(L, R, kc, F, st);
+}
+template <int MODE, class T, class P>
+__device__ __forceinline__ void roe_pick(RoeTag<1>, const T L[5], const T R[5],
+                                         const KConst<T, P>& kc, T F[5], uint32_t& st) {
+    RoeIO<T> a, b;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        a.v[q] = L[q];
+        b.v[q] = R[q];
+    }
+    a.st = b.st = 0;
+    const RoeIO<T> r = roe_call<MODE>(a, b, kc);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = r.v[q];
+    st |= r.st;
+}
+template <int MODE, int OOL, class T, class P>
+__device__ __forceinline__ void roe_solve(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                          T F[5], uint32_t& st) {
+    roe_pick<MODE>(RoeTag<OOL>(), L, R, kc, F, st);
+}
+
 // ---------------------------------------------------------------------------
 // Conserved state of a primitive face value.
 template <class T>
@@ -284,22 +327,18 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
     for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
     bool ok = true;
 #pragma unroll
-    for (int f = 0; f < 6; ++f)
-        ok = ok && admissible<MODE>(fs[f][0] + du[0], fs[f][1] + du[1], fs[f][2] + du[2],
-                                    fs[f][3] + du[3], fs[f][4] + du[4]);
-    if (ok) {
+    for (int f = 0; f < 6; ++f) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
+        ok = ok && admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4]);
+    }
+    if (!ok) {
+        st |= GAMER_ST_PREDICTOR_FALLBACK;
 #pragma unroll
         for (int f = 0; f < 6; ++f)
 #pragma unroll
-            for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
-    } else {
-        st |= GAMER_ST_PREDICTOR_FALLBACK;
-        if (kc.pfb == 0) {
-#pragma unroll
-            for (int f = 0; f < 6; ++f)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) fs[f][q] = uc[q];
-        }
+            for (int q = 0; q < 5; ++q)
+                fs[f][q] = (kc.pfb == 0) ? uc[q] : fs[f][q] - du[q];  // option 1: un-evolved
     }
 }
 
@@ -374,7 +413,7 @@ template <> struct SumAcc<float> {
 // ---------------------------------------------------------------------------
 // MINB: CTAs per SM the register budget is sized for (launch bounds); the
 // launcher picks the variant (2: no spills, 3: more warps per SM).
-template <int MODE, int MINB>
+template <int MODE, int MINB, int OOL = 0>
 __global__ void __launch_bounds__(kThreads, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
@@ -411,6 +450,15 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const int si = (side == 0) ? -1 : (side == 1) ? 16 : st_;
     const int sj = (side == 2) ? -1 : (side == 3) ? 16 : st_;
     const int psl = (sj + 2) * 20 + (si + 2);
+    // second prediction item of every thread: its second column (warps 0-2) or
+    // its slab cell (warps 3-4).  Both kinds store all four x/y faces; a slab
+    // cell's three unused faces go to entries 272..287 of their arrays, which
+    // nothing reads, so one code path serves both.
+    const int pc_b = two ? pc1 : psl;
+    const int o_xm = two ? fa1 : (side == 1 ? 256 + st_ : 272 + st_);
+    const int o_xp = two ? fa1 : (side == 0 ? 256 + st_ : 272 + st_);
+    const int o_ym = two ? fa1 : (side == 3 ? 256 + st_ : 272 + st_);
+    const int o_yp = two ? fa1 : (side == 2 ? 256 + st_ : 272 + st_);
 
     const T igm1 = T(1) / kc.gm1;
 
@@ -463,15 +511,81 @@ __global__ void __launch_bounds__(kThreads, MINB)
             T smax = T(0);
             SumAcc<T> sums;
 
-            for (int k = -1; k <= 16; ++k) {
+            // Per plane k, two barriers: phase CA runs C(k-1) -- finish plane
+            // k-2 and set up plane k-1 from the fluxes of phase B(k-1) -- then
+            // A(k), the half-step prediction of plane k; phase B(k) solves the
+            // Riemann problems of plane k and converts plane k+2.  C only reads
+            // what B wrote and A only writes what B reads next, so C(k-1) and
+            // A(k) share a phase.
+            T zm0[5], zm1[5], zpn0[5], zpn1[5], uc0[5], uc1[5], fz0[5], fz1[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                zm0[q] = zm1[q] = zpn0[q] = zpn1[q] = uc0[q] = uc1[q] = fz0[q] = fz1[q] = T(0);
+            for (int k = -1; k <= 17; ++k) {
                 const T* Wm = S.W[(k + 1) % 3];
                 const T* W0 = S.W[(k + 2) % 3];
                 const T* Wp = S.W[(k + 3) % 3];
                 const T* Uk = S.raw[(k + 2) & 1];
                 const bool inner = (k >= 0 && k <= 15);
 
-                // ---- phase A: half-step prediction of plane k
-                T zm0[5], zm1[5], zpn0[5], zpn1[5], uc0[5], uc1[5];
+                // ---- phase CA, part C(k-1): finish plane k-2, set up plane k-1
+                if (k - 1 >= 1) {
+                    const int kk = k - 2;
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cc == 1 && !two) break;
+                        const T* Ep = cc ? E1 : E0;
+                        const T* fo = cc ? fzo1 : fzo0;
+                        const T* fn = cc ? fz1 : fz0;
+                        const int jj = cc ? j1 : j0;
+                        T o[5];
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            o[q] = Ep[q] - lam * (fn[q] - fo[q]);
+                            gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
+                        }
+                        // epilogue: positivity flag, signal speed and sums
+                        const T ir = rcp_(o[0]);
+                        const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                        if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
+                        const T c2 = kc.gamma * p * ir;
+                        const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
+                        const T sp =
+                            max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
+                        if (sp > smax) smax = sp;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
+                    }
+                }
+                if (k - 1 >= 0 && k - 1 <= 15) {
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cc == 1 && !two) break;
+                        const int jj = cc ? j1 : j0;
+                        const int fa = cc ? fa1 : fa0;
+                        const int rxp = (i0 == 15) ? (256 + jj) : (fa + 1);
+                        const int ryp = 272 + ((jj == 15) ? (256 + i0) : (frow(jj + 1) * 16 + i0));
+                        const T* uc = cc ? uc1 : uc0;
+                        T* Ec = cc ? E1 : E0;
+                        T* fo = cc ? fzo1 : fzo0;
+                        const T* fn = cc ? fz1 : fz0;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            const T* fq = S.fxy + q * kFluxStride;
+                            const T D = (fq[rxp] - fq[fa]) + (fq[ryp] - fq[272 + fa]);
+                            Ec[q] = uc[q] - lam * D;
+                            fo[q] = fn[q];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    zp0[q] = zpn0[q];
+                    zp1[q] = zpn1[q];
+                }
+                if (k == 17) break;  // plane 15 is finished; nothing left to predict
+
+                // ---- phase CA, part A(k): half-step prediction of plane k
                 {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
@@ -492,48 +606,24 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         zpn0[q] = fs[5][q];
                     }
                 }
-                if (two) {
+                if (two || inner) {
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc1];
+                    for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc_b];
                     T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, uc1, pc1, half_lam, igm1, kc, fs, st);
+                    predict<MODE>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs, st);
                     if (inner) {
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
-                            S.xm[q * kFaceStride + fa1] = fs[0][q];
-                            S.xp[q * kFaceStride + fa1] = fs[1][q];
-                            S.ym[q * kFaceStride + fa1] = fs[2][q];
-                            S.yp[q * kFaceStride + fa1] = fs[3][q];
+                            S.xm[q * kFaceStride + o_xm] = fs[0][q];
+                            S.xp[q * kFaceStride + o_xp] = fs[1][q];
+                            S.ym[q * kFaceStride + o_ym] = fs[2][q];
+                            S.yp[q * kFaceStride + o_yp] = fs[3][q];
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < 5; ++q) {
                         zm1[q] = fs[4][q];
                         zpn1[q] = fs[5][q];
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) zm1[q] = zpn1[q] = uc1[q] = T(0);
-                    if (inner) {
-                        T us[5];
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) us[q] = Uk[q * kPlane + psl];
-                        T fs[6][5];
-                        predict<MODE>(Wm, W0, Wp, us, psl, half_lam, igm1, kc, fs, st);
-                        const int p = kFaceStride - 16 + st_;
-                        if (side == 0) {
-#pragma unroll
-                            for (int q = 0; q < 5; ++q) S.xp[q * kFaceStride + p] = fs[1][q];
-                        } else if (side == 1) {
-#pragma unroll
-                            for (int q = 0; q < 5; ++q) S.xm[q * kFaceStride + p] = fs[0][q];
-                        } else if (side == 2) {
-#pragma unroll
-                            for (int q = 0; q < 5; ++q) S.yp[q * kFaceStride + p] = fs[3][q];
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 5; ++q) S.ym[q * kFaceStride + p] = fs[2][q];
-                        }
                     }
                 }
                 __syncthreads();
@@ -543,15 +633,14 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     pending |= 1u << ((k + 2) & 1);
                 }
 
-                // ---- phase B: Riemann solves
-                T fz0[5], fz1[5];
+                // ---- phase B(k): Riemann solves
                 if (k >= 0) {
                     // z faces k-1/2 of the owned columns: rotated (rho, m_z, m_x, m_y, E)
                     {
                         T L[5] = {zp0[0], zp0[3], zp0[1], zp0[2], zp0[4]};
                         T R[5] = {zm0[0], zm0[3], zm0[1], zm0[2], zm0[4]};
                         T F[5];
-                        roe_rot<MODE>(L, R, kc, F, st);
+                        roe_solve<MODE, OOL>(L, R, kc, F, st);
                         fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
                         if (gff && (k == 0 || k == 16)) {
                             T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j0 * 16 + i0;
@@ -563,16 +652,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T L[5] = {zp1[0], zp1[3], zp1[1], zp1[2], zp1[4]};
                         T R[5] = {zm1[0], zm1[3], zm1[1], zm1[2], zm1[4]};
                         T F[5];
-                        roe_rot<MODE>(L, R, kc, F, st);
+                        roe_solve<MODE, OOL>(L, R, kc, F, st);
                         fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
                         if (gff && (k == 0 || k == 16)) {
                             T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j1 * 16 + i0;
 #pragma unroll
                             for (int q = 0; q < 5; ++q) dst[q * 256] = fz1[q];
                         }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) fz1[q] = T(0);
                     }
                 }
                 if (inner) {
@@ -617,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         R[2] = RA[c2 * kFaceStride + hi];
                         R[3] = RA[c3 * kFaceStride + hi];
                         R[4] = RA[4 * kFaceStride + hi];
-                        roe_rot<MODE>(L, R, kc, F, st);
+                        roe_solve<MODE, OOL>(L, R, kc, F, st);
                         S.fxy[wr] = F[0];
                         S.fxy[c1 * kFluxStride + wr] = F[1];
                         S.fxy[c2 * kFluxStride + wr] = F[2];
@@ -635,65 +721,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         }
                     }
                 }
-                __syncthreads();
-
-                // ---- phase C: finish plane k-1, set up plane k, convert plane k+2
-                if (k >= 1) {
-                    const int kk = k - 1;
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        if (cc == 1 && !two) break;
-                        const T* Ep = cc ? E1 : E0;
-                        const T* fo = cc ? fzo1 : fzo0;
-                        const T* fn = cc ? fz1 : fz0;
-                        const int jj = cc ? j1 : j0;
-                        T o[5];
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) {
-                            o[q] = Ep[q] - lam * (fn[q] - fo[q]);
-                            gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
-                        }
-                        // epilogue: positivity flag, signal speed and sums
-                        const T ir = rcp_(o[0]);
-                        const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
-                        if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
-                        const T c2 = kc.gamma * p * ir;
-                        const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
-                        const T sp =
-                            max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
-                        if (sp > smax) smax = sp;
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
-                    }
-                }
-                if (inner) {
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        if (cc == 1 && !two) break;
-                        const int jj = cc ? j1 : j0;
-                        const int fa = cc ? fa1 : fa0;
-                        const int rxp = (i0 == 15) ? (256 + jj) : (fa + 1);
-                        const int ryp = 272 + ((jj == 15) ? (256 + i0) : (frow(jj + 1) * 16 + i0));
-                        const T* uc = cc ? uc1 : uc0;
-                        T* Ec = cc ? E1 : E0;
-                        T* fo = cc ? fzo1 : fzo0;
-                        const T* fn = cc ? fz1 : fz0;
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) {
-                            const T* fq = S.fxy + q * kFluxStride;
-                            const T D = (fq[rxp] - fq[fa]) + (fq[ryp] - fq[272 + fa]);
-                            Ec[q] = uc[q] - lam * D;
-                            fo[q] = fn[q];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    zp0[q] = zpn0[q];
-                    zp1[q] = zpn1[q];
-                }
+                // plane k+2 -> primitives (into the slot of plane k-1)
                 if (k <= 15) {
-                    const int slot = (k + 2) & 1;  // slot of plane k+2
+                    const int slot = (k + 2) & 1;
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);

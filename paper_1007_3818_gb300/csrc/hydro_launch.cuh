@@ -8,6 +8,9 @@ namespace gamer {
 
 // Launch-shape override (0 = automatic: every SM filled to its occupancy).
 int& hydro_ctas_per_sm_override(int mode);
+// Code-shape variant of the FP32 kernel (0: inline Riemann solver, 1: one
+// out-of-line copy); chosen by the autotuner.
+int& hydro_variant();
 
 template <int MODE>
 int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
@@ -47,6 +50,10 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                  KConst<T, P>);
     if constexpr (MODE == GAMER_MODE_F64) {
         kern = hydro_step_kernel<MODE, 1>;
+    } else if constexpr (MODE == GAMER_MODE_F32) {
+        kern = (minb == 2) ? hydro_step_kernel<MODE, 2>
+                           : (hydro_variant() == 1 ? hydro_step_kernel<MODE, 3, 1>
+                                                   : hydro_step_kernel<MODE, 3>);
     } else {
         kern = (minb == 2) ? hydro_step_kernel<MODE, 2> : hydro_step_kernel<MODE, 3>;
     }

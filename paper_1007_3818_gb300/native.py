@@ -73,6 +73,8 @@ def lib():
         L.gamer_device_check.restype = ctypes.c_int
         L.gamer_version.argtypes = []
         L.gamer_version.restype = ctypes.c_char_p
+        L.gamer_set_hydro_variant.argtypes = [i32]
+        L.gamer_set_hydro_variant.restype = ctypes.c_int
         L.gamer_set_hydro_ctas_per_sm.argtypes = [i32, i32]
         L.gamer_set_hydro_ctas_per_sm.restype = ctypes.c_int
         L.gamer_microbench.argtypes = [i32, i64, vp, i64, P(d), vp]
@@ -247,6 +249,10 @@ def gamer_version():
 def gamer_set_hydro_ctas_per_sm(mode, ctas_per_sm):
     _check(lib().gamer_set_hydro_ctas_per_sm(int(mode), int(ctas_per_sm)),
            "gamer_set_hydro_ctas_per_sm")
+
+
+def gamer_set_hydro_variant(variant):
+    _check(lib().gamer_set_hydro_variant(int(variant)), "gamer_set_hydro_variant")
 
 
 def gamer_microbench(kind, iters, buf, n=0, stream=None):

@@ -57,16 +57,27 @@ def tune_hydro(mode, inp, out, face_flux, dt, dh, status, partials, params, reps
     key = (torch.cuda.get_device_name(), int(mode), _bucket(int(inp.shape[0])))
     if key in _cache:
         native.gamer_set_hydro_ctas_per_sm(mode, _cache[key]["ctas_per_sm"])
+        native.gamer_set_hydro_variant(_cache[key]["variant"])
         return _cache[key]
-    candidates = [1] if mode == native.GAMER_MODE_F64 else [1, 2, 3]
+    # (CTAs per SM, code variant): the FP32 3-CTA build also comes with the
+    # Riemann solver out of line (smaller code for the instruction cache)
+    if mode == native.GAMER_MODE_F64:
+        candidates = [(1, 0)]
+    elif mode == native.GAMER_MODE_F32:
+        candidates = [(2, 0), (3, 0), (3, 1)]
+    else:
+        candidates = [(2, 0), (3, 0)]
     results = {}
-    for c in candidates:
+    for c, v in candidates:
         native.gamer_set_hydro_ctas_per_sm(mode, c)
-        results[c] = _time(lambda: native.hydro_advance(mode, inp, out, face_flux, dt, dh, status,
-                                                        partials, params), reps)
+        native.gamer_set_hydro_variant(v)
+        results[(c, v)] = _time(lambda: native.hydro_advance(mode, inp, out, face_flux, dt, dh,
+                                                             status, partials, params), reps)
     best = min(results, key=results.get)
-    native.gamer_set_hydro_ctas_per_sm(mode, best)
-    res = {"ctas_per_sm": best, "ms": results[best], "all": results}
+    native.gamer_set_hydro_ctas_per_sm(mode, best[0])
+    native.gamer_set_hydro_variant(best[1])
+    res = {"ctas_per_sm": best[0], "variant": best[1], "ms": results[best],
+           "all": {f"{c}x{v}": t for (c, v), t in results.items()}}
     _cache[key] = res
     if cache_path:
         _save(cache_path, key, res)
