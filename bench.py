@@ -36,10 +36,12 @@ CFL = 0.5
 SEED = 1007
 NCELLS = 256          # level edge in cells
 GROUP_CELLS = 4096
-# algorithmic bytes of one group update: in 20^3x5, out 16^3x5, face flux
-# 6x5x16^2 (element size), dt, dh (8 B each), status (4 B), partials (48 B)
+# algorithmic HBM bytes of one group update by the fused level kernel: its
+# 16^3x5 interior read once (neighbours' ghost cells are re-reads served by
+# L2), 16^3x5 out and 6x5x16^2 face flux written (element size), dt, dh
+# (8 B each), status (4 B), partials (48 B)
 def group_bytes(esz):
-    return (40000 + 20480 + 7680) * esz + 16 + 4 + 48
+    return (20480 + 20480 + 7680) * esz + 16 + 4 + 48
 
 
 SM_COUNT = 152
@@ -319,18 +321,22 @@ def main():
     # autotuned launch shape (register/smem variant and CTAs per SM) on this batch
     from paper_1007_3818_gb300 import tune
     tuned = tune.tune_hydro(mode, tiles, level_b, ff, dt_g, dh_g, status, partials, params)
+    tuned_level = tune.tune_hydro_level(mode, level_a, level_b, ff, gx, gy, gz, 0, dt_g, dh_g,
+                                        status, partials, params)
 
     cur, nxt = [level_a, level_b], 0
     ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
     def step(i=None):
+        # one level step: hydro step with the ghost gather fused in, then the
+        # FP64 dt / conservation reduction that feeds the next step's dt
         nonlocal nxt
         src, dst = cur[nxt], cur[1 - nxt]
-        fill(src, tiles, gx, gy, gz, 0)
         if i is not None:
             ev_a[i].record(stream)
-        native.hydro_advance(mode, tiles, dst, ff, dt_g, dh_g, status, partials, params)
+        native.hydro_advance_level(mode, src, dst, ff, gx, gy, gz, 0, dt_g, dh_g, status,
+                                   partials, params)
         if i is not None:
             ev_b[i].record(stream)
         native.gamer_hydro_dt(partials, None, dh_level, CFL, dt_level, totals, dt_g, ws)
@@ -362,9 +368,9 @@ def main():
     value = world * cells_per_step * args.steps / el
 
     # CUDA-graph replay of the same step (A -> B, B -> A alternating)
-    graphs = [native.LevelGraph(mode, cur[0], cur[1], tiles, ff, dt_g, dh_g, status, partials,
+    graphs = [native.LevelGraph(mode, cur[0], cur[1], None, ff, dt_g, dh_g, status, partials,
                                 gx, gy, gz, 0, params, dh_level, dt_level, totals, ws),
-              native.LevelGraph(mode, cur[1], cur[0], tiles, ff, dt_g, dh_g, status, partials,
+              native.LevelGraph(mode, cur[1], cur[0], None, ff, dt_g, dh_g, status, partials,
                                 gx, gy, gz, 0, params, dh_level, dt_level, totals, ws)]
     nsteps_done = args.warmup + args.steps  # parity of the buffer holding the state
     gi = nsteps_done % 2
@@ -426,7 +432,8 @@ def main():
     roofline_hbm = {
         "bound": "hbm", "achieved": G * group_bytes(esz) / adv_s / 1e9, "peak": hbm_peak,
         "unit": "GB/s", "frac": G * group_bytes(esz) / adv_s / 1e9 / hbm_peak,
-        "traffic": None, "note": "algorithmic bytes of the hydro kernel vs measured HBM copy"}
+        "traffic": None, "note": "algorithmic bytes of the fused hydro kernel (level in, "
+                                 "state and face fluxes out) vs measured HBM copy"}
     if flops_per_cell is not None:
         ach = flops_per_cell * cells_per_step / adv_s / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
@@ -441,19 +448,22 @@ def main():
             "dtype": {"f32": "f32", "mixed": "f32+f64", "f64": "f64"}[args.mode],
             "data": "synthetic",
             "config": {"workload": "uniform periodic level, 4096 patch groups of 16^3 cells "
-                                   "(256^3), ghost fill + MUSCL-Hancock/Roe step + FP64 dt "
-                                   "reduction per step",
+                                   "(256^3), MUSCL-Hancock/Roe step with the ghost gather "
+                                   "fused in + FP64 dt reduction per step",
                        "mode": args.mode, "groups": G, "cells_per_step": cells_per_step,
                        "gamma": GAMMA, "cfl": CFL, "seed": SEED,
-                       "l2": "inputs larger than L2 (tiles %.0f MB per step)" %
-                             (G * 40000 * esz / 1e6),
+                       "l2": "inputs larger than L2 (level %.0f MB read, %.0f MB written "
+                             "per step)" % (G * 20480 * esz / 1e6, G * 28160 * esz / 1e6),
                        "parallelism": f"{world} independent levels (weak scaling)"},
             "roofline": roofline, "roofline_hbm": roofline_hbm, "cpu_baseline": cpu,
             "e2e": e2e, "clocks": clk,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "kernel_ms": {"hydro_step": adv_ms},
-            "tuned": {"ctas_per_sm": tuned["ctas_per_sm"], "variant": tuned["variant"],
-                      "candidates_ms": tuned["all"]},
+            "tuned": {"ctas_per_sm": tuned_level["ctas_per_sm"],
+                      "variant": tuned_level["variant"], "candidates_ms": tuned_level["all"],
+                      "tiles_kernel": {"ctas_per_sm": tuned["ctas_per_sm"],
+                                       "variant": tuned["variant"],
+                                       "candidates_ms": tuned["all"]}},
             "graph": {"ms_per_step": el_graph / args.steps * 1e3,
                       "value": world * cells_per_step * args.steps / el_graph},
             "status_or": int(np.bitwise_or.reduce(st)),

@@ -108,6 +108,34 @@ int gamer_hydro_advance_f64(const double* in, double* out, double* face_flux, co
                             const gh_params* p, void* stream);
 
 /*
+ * gamer_hydro_advance_level_{f32,mixed,f64}: the same step for every group of
+ * a uniform level, with the ghost-zone preparation fused into the solver: each
+ * group's 20^3 input is gathered plane by plane from its own 16^3 interior and
+ * its neighbours' (periodic or zero-gradient boundaries, as
+ * gamer_fill_ghosts_uniform_*), so no 20^3 tiles are written or read.
+ *   level     [G][5][16][16][16], G = gx*gy*gz, group id (z*gy + y)*gx + x;
+ *             16-byte aligned; must not overlap out (every group reads its
+ *             neighbours' interiors).
+ *   out, face_flux, dt, dh, status, partials: as gamer_hydro_advance_* with
+ *             N = G.
+ *   bc        0 periodic, 1 zero-gradient.
+ * Results equal gamer_fill_ghosts_uniform_* followed by gamer_hydro_advance_*
+ * bit for bit.
+ */
+int gamer_hydro_advance_level_f32(const float* level, float* out, float* face_flux, int32_t gx,
+                                  int32_t gy, int32_t gz, int32_t bc, const double* dt,
+                                  const double* dh, uint32_t* status, double* partials,
+                                  const gh_params* p, void* stream);
+int gamer_hydro_advance_level_mixed(const float* level, float* out, float* face_flux,
+                                    int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                    const double* dt, const double* dh, uint32_t* status,
+                                    double* partials, const gh_params* p, void* stream);
+int gamer_hydro_advance_level_f64(const double* level, double* out, double* face_flux,
+                                  int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                  const double* dt, const double* dh, uint32_t* status,
+                                  double* partials, const gh_params* p, void* stream);
+
+/*
  * gamer_fill_ghosts_uniform_{f32,f64}: ghost-zone preparation for a uniform
  * level (paper Sec. 2: the ghost-zone data each patch needs before the solver
  * runs).  level[G][5][16][16][16] holds the interiors of G = gx*gy*gz groups,
@@ -172,8 +200,10 @@ int gamer_hydro_dt_noalloc(const double* partials, int64_t N, const int32_t* lev
  * gamer_hydro_dt, whose dt_group output is the dt[] input of the next step.
  * A run of steps alternates this graph with the one created with level_a and
  * level_b swapped.  All pointers are caller-owned device arrays sized for
- * G = gx*gy*gz groups: level_a, level_b [G][5][16]^3 and tiles [G][5][20]^3 of
- * the mode's element type; face_flux [G][6][5][16][16] or NULL; dt_group,
+ * G = gx*gy*gz groups: level_a, level_b [G][5][16]^3 of the mode's element
+ * type; tiles [G][5][20]^3 for a separate ghost-fill kernel, or NULL to fuse
+ * the ghost gather into the step kernel (gamer_hydro_advance_level_*);
+ * face_flux [G][6][5][16][16] or NULL; dt_group,
  * dh_group [G]; status [G] or NULL; partials [G][6]; dh_level, dt_level [1];
  * totals [5] or NULL; workspace of gamer_hydro_dt_workspace_bytes(G, 1) bytes.
  * dt_group must hold the first step's dt before the first launch.
@@ -262,9 +292,11 @@ const char* gamer_version(void);
  * process-wide setting. */
 int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
 
-/* Code shape of the FP32 hydro kernel's 3-CTA build: 0 = Riemann solver
- * inlined at each call site (default), 1 = one out-of-line copy (smaller code,
- * a call per solve).  Used by the autotuner; process-wide setting. */
+/* Code shape of the hydro kernel: 0 = one problem at a time per thread
+ * (default); 1 = as 0 with one out-of-line copy of the Riemann solver (FP32
+ * 3-CTA build only); 2 = two interleaved problems per thread (z-face states in
+ * shared memory, branch-free Roe path, compile-time limiter; 2 CTAs per SM in
+ * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide setting. */
 int gamer_set_hydro_variant(int32_t variant);
 
 /* Throughput probes for the roofline denominators (not part of the scheme).

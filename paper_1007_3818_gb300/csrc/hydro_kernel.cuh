@@ -98,13 +98,16 @@ __device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
     }
 }
 
-template <class T, class P>
+// LIM >= 0 fixes the limiter at compile time (no branch per slope); LIM < 0
+// reads it from kc.limiter.
+template <int LIM = -1, class T, class P>
 __device__ __forceinline__ T limit(T a, T b, const KConst<T, P>& kc) {
     const T ab = a * b;
+    const int lim = (LIM >= 0) ? LIM : kc.limiter;
     T r;
-    if (kc.limiter == 1) {
+    if (lim == 1) {
         r = (a > T(0)) ? min_(a, b) : max_(a, b);
-    } else if (kc.limiter == 2) {
+    } else if (lim == 2) {
         T m = min_(T(2) * abs_(a), T(2) * abs_(b));
         m = min_(m, T(0.5) * abs_(a + b));
         r = (a > T(0)) ? m : -m;
@@ -215,13 +218,131 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
     F[4] = T(0.5) * (FL[4] + FR[4]) - T(0.5) * D4;
 }
 
-// Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
-// states and flux travel by value, the status bits come back in the result.
+// Branch-free Roe flux (rotated frame, as roe_rot) without the fallback:
+// returns true when the HLLE fallback must replace F (Roe sound speed squared
+// not positive, or an intermediate state with rho <= 0 or p <= 0).  Having no
+// branch, two calls in a row are scheduled as one block of independent work.
+template <int MODE, class T, class P>
+__device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                         T F[5]) {
+    const T irL = rcp_(L[0]), irR = rcp_(R[0]);
+    const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
+    const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
+    const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
+    const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
+    const T mL = L[0] * uL, mR = R[0] * uR;
+    const T cL = sqrt_(kc.gamma * pL * irL);
+    const T cR = sqrt_(kc.gamma * pR * irR);
+    const T HL = (L[4] + pL) * irL;
+    const T HR = (R[4] + pR) * irR;
+    const T rr = sqrt_(R[0] * irL);
+    const T i1 = rcp_(T(1) + rr);
+    const T uT = (uL + rr * uR) * i1;
+    const T vT = (vL + rr * vR) * i1;
+    const T wT = (wL + rr * wR) * i1;
+    const T HT = (HL + rr * HR) * i1;
+    const T q2 = uT * uT + vT * vT + wT * wT;
+    const T cT2 = kc.gm1 * (HT - T(0.5) * q2);
+    const T cT = sqrt_(cT2);
+    const T rT = rr * L[0];
+    const T dr = R[0] - L[0], du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
+    const T ic2 = rcp_(cT2);
+    const T a1 = (dp - rT * cT * du) * (T(0.5) * ic2);
+    const T a2 = dr - dp * ic2;
+    const T a3 = rT * dv;
+    const T a4 = rT * dw;
+    const T a5 = (dp + rT * cT * du) * (T(0.5) * ic2);
+    const T K1u = uT - cT, K5u = uT + cT;
+    const T K1E = HT - uT * cT, K5E = HT + uT * cT;
+    const T s1r = L[0] + a1, s1n = L[1] + a1 * K1u, s1a = L[2] + a1 * vT, s1b = L[3] + a1 * wT,
+            s1E = L[4] + a1 * K1E;
+    const T s4r = R[0] - a5, s4n = R[1] - a5 * K5u, s4a = R[2] - a5 * vT, s4b = R[3] - a5 * wT,
+            s4E = R[4] - a5 * K5E;
+    const T is1 = rcp_(s1r), is4 = rcp_(s4r);
+    const T p1 = pressure<MODE>(s1r, s1n, s1a, s1b, s1E, is1, kc);
+    const T p4 = pressure<MODE>(s4r, s4n, s4a, s4b, s4E, is4, kc);
+    const bool fallback = !(cT2 > T(0) && s1r > T(0) && p1 > T(0) && s4r > T(0) && p4 > T(0));
+    const T l1s = s1n * is1 - sqrt_(kc.gamma * p1 * is1);
+    const T l5s = s4n * is4 + sqrt_(kc.gamma * p4 * is4);
+    const T d1 = max_(T(0), max_(K1u - (uL - cL), l1s - K1u));
+    const T d5 = max_(T(0), max_(K5u - l5s, (uR + cR) - K5u));
+    T e1 = abs_(K1u), e5 = abs_(K5u);
+    const T f1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
+    const T f5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
+    e1 = (e1 < d1) ? f1 : e1;
+    e5 = (e5 < d5) ? f5 : e5;
+    const T e2 = abs_(uT);
+    const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
+    const T D0 = s1 + s2 + s5;
+    const T D1 = s1 * K1u + s2 * uT + s5 * K5u;
+    const T D2 = s1 * vT + s2 * vT + s3 + s5 * vT;
+    const T D3 = s1 * wT + s2 * wT + s4 + s5 * wT;
+    const T D4 = s1 * K1E + s2 * (T(0.5) * q2) + s3 * vT + s4 * wT + s5 * K5E;
+    F[0] = T(0.5) * (mL + mR) - T(0.5) * D0;
+    F[1] = T(0.5) * ((mL * uL + pL) + (mR * uR + pR)) - T(0.5) * D1;
+    F[2] = T(0.5) * (mL * vL + mR * vR) - T(0.5) * D2;
+    F[3] = T(0.5) * (mL * wL + mR * wR) - T(0.5) * D3;
+    F[4] = T(0.5) * ((L[4] + pL) * uL + (R[4] + pR) * uR) - T(0.5) * D4;
+    return fallback;
+}
+
+// The HLLE fallback recomputed from the two states alone (rare path, one
+// out-of-line copy): Einfeldt speeds with the Roe speeds when c~^2 > 0.
 template <class T>
 struct RoeIO {
     T v[5];
     uint32_t st;
 };
+template <int MODE, class T, class P>
+__device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P> kc) {
+    const T* L = Li.v;
+    const T* R = Ri.v;
+    const T irL = rcp_(L[0]), irR = rcp_(R[0]);
+    const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
+    const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
+    const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
+    const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
+    T FL[5], FR[5];
+    const T mL = L[0] * uL, mR = R[0] * uR;
+    FL[0] = mL; FL[1] = mL * uL + pL; FL[2] = mL * vL; FL[3] = mL * wL; FL[4] = (L[4] + pL) * uL;
+    FR[0] = mR; FR[1] = mR * uR + pR; FR[2] = mR * vR; FR[3] = mR * wR; FR[4] = (R[4] + pR) * uR;
+    const T cL = sqrt_(kc.gamma * pL * irL);
+    const T cR = sqrt_(kc.gamma * pR * irR);
+    const T rr = sqrt_(R[0] * irL);
+    const T i1 = rcp_(T(1) + rr);
+    const T uT = (uL + rr * uR) * i1, vT = (vL + rr * vR) * i1, wT = (wL + rr * wR) * i1;
+    const T HT = ((L[4] + pL) * irL + rr * ((R[4] + pR) * irR)) * i1;
+    const T cT2 = kc.gm1 * (HT - T(0.5) * (uT * uT + vT * vT + wT * wT));
+    T sl = uL - cL, sr = uR + cR;
+    if (cT2 > T(0)) {
+        const T cT = sqrt_(cT2);
+        sl = min_(sl, uT - cT);
+        sr = max_(sr, uT + cT);
+    }
+    RoeIO<T> out;
+    hlle_rot(L, R, FL, FR, sl, sr, out.v);
+    out.st = GAMER_ST_HLLE_FALLBACK;
+    return out;
+}
+
+template <int MODE, class T, class P>
+__device__ __forceinline__ void hlle_apply(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                           T F[5], uint32_t& st) {
+    RoeIO<T> a, b;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        a.v[q] = L[q];
+        b.v[q] = R[q];
+    }
+    a.st = b.st = 0;
+    const RoeIO<T> r = hlle_full<MODE>(a, b, kc);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = r.v[q];
+    st |= r.st;
+}
+
+// Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
+// states and flux travel by value, the status bits come back in the result.
 template <int MODE, class T, class P>
 __device__ __noinline__ RoeIO<T> roe_call(RoeIO<T> L, RoeIO<T> R, KConst<T, P> kc) {
     RoeIO<T> out;
@@ -293,14 +414,15 @@ __device__ __forceinline__ void flux_diff(const T wm[5], T Em, const T wp[5], T 
 }
 
 // Hancock half-step for the cell at plane index c (20x20 plane layout) of
-// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1; uc the cell's
-// conserved state.  fs[f] receives the conserved face states x-, x+, y-, y+,
-// z-, z+.
-template <int MODE, class T, class P>
-__device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
-                                        const T* __restrict__ Wp, const T uc[5], int c,
-                                        T half_lam, T igm1, const KConst<T, P>& kc,
-                                        T fs[6][5], uint32_t& st) {
+// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1.  Branch-free part:
+// fs[f] receives the evolved conserved face states x-, x+, y-, y+, z-, z+,
+// du the common half-step increment; returns whether all six are admissible
+// (rho > 0, p > 0).
+template <int MODE, int LIM, class T, class P>
+__device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* __restrict__ W0,
+                                             const T* __restrict__ Wp, int c, T half_lam,
+                                             T igm1, const KConst<T, P>& kc, T fs[6][5],
+                                             T du[5]) {
     T wc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) wc[q] = W0[q * kPlane + c];
@@ -312,7 +434,7 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
         T wm[5], wp[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            const T s = limit(wc[q] - lo[q * kPlane], hi[q * kPlane] - wc[q], kc);
+            const T s = limit<LIM>(wc[q] - lo[q * kPlane], hi[q * kPlane] - wc[q], kc);
             wm[q] = wc[q] - T(0.5) * s;
             wp[q] = wc[q] + T(0.5) * s;
         }
@@ -322,7 +444,6 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
         if (d == 1) flux_diff<1>(wm, fs[2][4], wp, fs[3][4], acc);
         if (d == 2) flux_diff<2>(wm, fs[4][4], wp, fs[5][4], acc);
     }
-    T du[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
     bool ok = true;
@@ -332,13 +453,29 @@ __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __res
         for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
         ok = ok && admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4]);
     }
-    if (!ok) {
+    return ok;
+}
+
+// Predictor fallback: all six states become the cell average (option 0) or
+// the un-evolved reconstruction, recovered as (U + du) - du (option 1).
+template <class T, class P>
+__device__ __forceinline__ void predict_fallback(const T uc[5], const T du[5],
+                                                 const KConst<T, P>& kc, T fs[6][5]) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) fs[f][q] = (kc.pfb == 0) ? uc[q] : fs[f][q] - du[q];
+}
+
+template <int MODE, int LIM = -1, class T, class P>
+__device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
+                                        const T* __restrict__ Wp, const T uc[5], int c,
+                                        T half_lam, T igm1, const KConst<T, P>& kc,
+                                        T fs[6][5], uint32_t& st) {
+    T du[5];
+    if (!predict_core<MODE, LIM>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du)) {
         st |= GAMER_ST_PREDICTOR_FALLBACK;
-#pragma unroll
-        for (int f = 0; f < 6; ++f)
-#pragma unroll
-            for (int q = 0; q < 5; ++q)
-                fs[f][q] = (kc.pfb == 0) ? uc[q] : fs[f][q] - du[q];  // option 1: un-evolved
+        predict_fallback(uc, du, kc, fs);
     }
 }
 
@@ -377,8 +514,10 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
     }
 }
 
-template <class T>
-__device__ __forceinline__ void issue_plane(Smem<T>& S, const T* gin, int kp) {
+// Copies input plane kp into its ring slot of any shared layout with raw[2][]
+// and mbar[2] members.
+template <class SM, class T>
+__device__ __forceinline__ void issue_plane(SM& S, const T* gin, int kp) {
     const int slot = (kp + 2) & 1;
     constexpr uint32_t bytes = 5u * kPlane * sizeof(T);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -388,6 +527,85 @@ __device__ __forceinline__ void issue_plane(Smem<T>& S, const T* gin, int kp) {
         bulk_copy_g2s(&S.raw[slot][q * kPlane], gin + (q * 20 + (kp + 2)) * kPlane,
                       kPlane * sizeof(T), &S.mbar[slot]);
 }
+
+// Uniform level read directly by the kernel (fused ghost gather): gx*gy*gz
+// groups of [5][16][16][16], group id (z*gy + y)*gx + x, periodic (bc 0) or
+// zero-gradient (bc 1) boundaries.
+struct LevelGeom {
+    int gx, gy, gz, bc;
+};
+
+__device__ __forceinline__ int wrap_coord(int X, int n, int bc) {
+    if (bc == 0) {
+        X %= n;
+        return X < 0 ? X + n : X;
+    }
+    return X < 0 ? 0 : (X >= n ? n - 1 : X);
+}
+
+// Builds input plane kp of group (bx, by, bz) in its ring slot straight from
+// the level: thread r < 100 copies row (v, j) = (r / 20, r % 20) -- the
+// group's 16 interior cells and the two x-ghost pairs of its neighbours -- in
+// 2-cell cp.async copies (single cells where a clamped boundary repeats one);
+// every thread then arrives on the slot's barrier (expected count kThreads).
+template <class SM, class T>
+__device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
+                                             const LevelGeom& L, int bx, int by, int bz,
+                                             int kp) {
+    const int slot = (kp + 2) & 1;
+    const int r = threadIdx.x;
+    if (r < 100) {
+        constexpr int PAIR = 2 * int(sizeof(T)), ONE = int(sizeof(T));
+        const int v = r / 20, j = r - v * 20;
+        const int nx = 16 * L.gx;
+        const int Z = wrap_coord(bz * 16 + kp, 16 * L.gz, L.bc);
+        const int Y = wrap_coord(by * 16 + j - 2, 16 * L.gy, L.bc);
+        const T* row = level + ((int64_t(Z >> 4) * L.gy + (Y >> 4)) * L.gx) * 20480 +
+                       v * 4096 + (Z & 15) * 256 + (Y & 15) * 16;
+        T* dst = &S.raw[slot][v * kPlane + j * 20];
+        const T* own = row + int64_t(bx) * 20480;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cp_async<PAIR>(dst + 2 + 2 * c, own + 2 * c);
+        const int xl0 = wrap_coord(bx * 16 - 2, nx, L.bc), xl1 = wrap_coord(bx * 16 - 1, nx, L.bc);
+        const int xr0 = wrap_coord(bx * 16 + 16, nx, L.bc), xr1 = wrap_coord(bx * 16 + 17, nx, L.bc);
+        const T* sl0 = row + int64_t(xl0 >> 4) * 20480 + (xl0 & 15);
+        const T* sl1 = row + int64_t(xl1 >> 4) * 20480 + (xl1 & 15);
+        const T* sr0 = row + int64_t(xr0 >> 4) * 20480 + (xr0 & 15);
+        const T* sr1 = row + int64_t(xr1 >> 4) * 20480 + (xr1 & 15);
+        if (xl1 == xl0 + 1) {
+            cp_async<PAIR>(dst, sl0);
+        } else {
+            cp_async<ONE>(dst, sl0);
+            cp_async<ONE>(dst + 1, sl1);
+        }
+        if (xr1 == xr0 + 1) {
+            cp_async<PAIR>(dst + 18, sr0);
+        } else {
+            cp_async<ONE>(dst + 18, sr0);
+            cp_async<ONE>(dst + 19, sr1);
+        }
+    }
+    cp_async_arrive(&S.mbar[slot]);
+}
+
+// Plane loaders by input kind (struct dispatch): 0 -- TMA bulk copies of the
+// tile's plane issued by thread 0; 1 -- gather from the level by 100 threads.
+template <int SRC> struct PlaneLoader;
+template <> struct PlaneLoader<0> {
+    template <class SM, class T>
+    static __device__ __forceinline__ void load(SM& S, const T* gin, const T*, const LevelGeom&,
+                                                int, int, int, int kp) {
+        if (threadIdx.x == 0) issue_plane(S, gin, kp);
+    }
+};
+template <> struct PlaneLoader<1> {
+    template <class SM, class T>
+    static __device__ __forceinline__ void load(SM& S, const T*, const T* level,
+                                                const LevelGeom& L, int bx, int by, int bz,
+                                                int kp) {
+        gather_plane(S, level, L, bx, by, bz, kp);
+    }
+};
 
 // Accumulator of the per-group conserved sums: FP64 in FP64 mode; in FP32
 // modes a compensated (hi, lo) float pair per thread (TwoSum), exact to about
@@ -413,14 +631,18 @@ template <> struct SumAcc<float> {
 // ---------------------------------------------------------------------------
 // MINB: CTAs per SM the register budget is sized for (launch bounds); the
 // launcher picks the variant (2: no spills, 3: more warps per SM).
-template <int MODE, int MINB, int OOL = 0>
+// SRC 0: `in` holds N ghost-padded 20^3 tiles, loaded plane by plane with the
+// TMA engine; SRC 1: `in` is the uniform level `geo` (N = gx*gy*gz groups) and
+// each plane is gathered from the group and its neighbours (fused ghost fill).
+template <int MODE, int MINB, int OOL = 0, int SRC = 0>
 __global__ void __launch_bounds__(kThreads, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
                       typename Prec<MODE>::T* __restrict__ face_flux,
                       const double* __restrict__ dt, const double* __restrict__ dh,
                       uint32_t* __restrict__ status, double* __restrict__ partials, int64_t N,
-                      KConst<typename Prec<MODE>::T, typename Prec<MODE>::P> kc) {
+                      KConst<typename Prec<MODE>::T, typename Prec<MODE>::P> kc,
+                      LevelGeom geo) {
     using T = typename Prec<MODE>::T;
     extern __shared__ __align__(128) unsigned char smem_bytes[];
     Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_bytes);
@@ -428,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const int lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], 1);
+        for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], SRC == 0 ? 1 : kThreads);
         mbar_init_fence();
     }
     __syncthreads();
@@ -464,6 +686,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
     for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
         const T* gin = in + g * 40000;
+        const int gbx = int(g % geo.gx), gby = int((g / geo.gx) % geo.gy),
+                  gbz = int(g / (int64_t(geo.gx) * geo.gy));
+        // one input plane into its ring slot (all threads call this)
+        auto load_plane = [&](int kp) {
+            PlaneLoader<SRC>::load(S, gin, in, geo, gbx, gby, gbz, kp);
+        };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * 7680 : nullptr;
         const double dtg = dt[g], dhg = dh[g];
@@ -474,9 +702,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
             S.status = 0;
             if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0))
                 st |= GAMER_ST_BAD_INPUT;
-            issue_plane(S, gin, -2);
-            issue_plane(S, gin, -1);
         }
+        load_plane(-2);
+        load_plane(-1);
         pending |= 3u;
         // prologue: planes -2, -1, 0 -> primitives; plane 0 reuses slot 0
         bool timed_out = false;
@@ -488,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
             timed_out = true;
         }
         if (__syncthreads_or(timed_out)) goto abort_group;
-        if (tid == 0) issue_plane(S, gin, 0);
+        load_plane(0);
         pending |= 1u;
         for (int s = 1; s >= 0; --s) {  // plane -1 (slot 1), then plane 0 (slot 0)
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
@@ -629,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 __syncthreads();
                 // plane k has been read: its slot takes plane k+2
                 if (k <= 15) {
-                    if (tid == 0) issue_plane(S, gin, k + 2);
+                    load_plane(k + 2);
                     pending |= 1u << ((k + 2) & 1);
                 }
 

@@ -3,6 +3,7 @@
 
 #include "abi_common.h"
 #include "hydro_kernel.cuh"
+#include "hydro_pair.cuh"
 
 namespace gamer {
 
@@ -12,11 +13,13 @@ int& hydro_ctas_per_sm_override(int mode);
 // out-of-line copy); chosen by the autotuner.
 int& hydro_variant();
 
-template <int MODE>
-int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
-                  typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
-                  uint32_t* status, double* partials, int64_t N, const gh_params* p,
-                  void* stream) {
+// Common launch path.  SRC 0: `in` = N tiles [N][5][20]^3; SRC 1: `in` = the
+// level `geo` (N = gx*gy*gz), ghosts gathered in the kernel.
+template <int MODE, int SRC>
+int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
+                 typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
+                 uint32_t* status, double* partials, int64_t N, const gh_params* p,
+                 LevelGeom geo, void* stream) {
     using T = typename Prec<MODE>::T;
     using P = typename Prec<MODE>::P;
     if (N < 0) return GAMER_E_PARAM;
@@ -27,7 +30,8 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     if (!aligned(in, 16) || !aligned(out, sizeof(T)) || !aligned(face_flux, sizeof(T)) ||
         !aligned(dt, 8) || !aligned(dh, 8) || !aligned(status, 4) || !aligned(partials, 8))
         return GAMER_E_ALIGN;
-    const size_t nin = size_t(N) * 40000 * sizeof(T), nout = size_t(N) * 20480 * sizeof(T);
+    const size_t nin = size_t(N) * (SRC == 0 ? 40000 : 20480) * sizeof(T);
+    const size_t nout = size_t(N) * 20480 * sizeof(T);
     const size_t nff = face_flux ? size_t(N) * 7680 * sizeof(T) : 0;
     const size_t nst = status ? size_t(N) * 4 : 0, npa = partials ? size_t(N) * 48 : 0;
     const void* ins[3] = {in, dt, dh};
@@ -43,19 +47,50 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     DeviceInfo dev = current_device();
     if (dev.status != GAMER_OK) return dev.status;
 
-    // variant: FP64 has one (1 CTA/SM); FP32 modes are built for 2 and 3 CTAs/SM
+    KConst<T, P> kc;
+    kc.gamma = T(p->gamma);
+    kc.gm1 = T(p->gamma - 1.0);
+    kc.gm1p = P(p->gamma - 1.0);
+    kc.limiter = p->limiter;
+    kc.pfb = p->predictor_fallback;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int want = hydro_ctas_per_sm_override(MODE);
-    const int minb = (MODE == GAMER_MODE_F64) ? 1 : ((want == 2) ? 2 : 3);
+    const int var = hydro_variant();
+
+    // variants: 0 -- one problem at a time, FP32 modes built for 3 (default)
+    // or 2 CTAs/SM, FP64 for 1; 1 (FP32 tiles only) -- the same with the
+    // Riemann solver out of line; 2 (tiles only) -- two interleaved problems
+    // per thread (pair kernel, 2 CTAs/SM in FP32, 1 in FP64), van Leer limiter
+    // compiled in plus a runtime-limiter build for the others.
+    if constexpr (SRC == 0) {
+      if (var == 2) {
+        constexpr int MB = (MODE == GAMER_MODE_F64) ? 1 : 2;
+        auto kern = (p->limiter == 0) ? hydro_pair_kernel<MODE, MB, 0>
+                                      : hydro_pair_kernel<MODE, MB, -1>;
+        const int smem = int(sizeof(SmemPair<T>));
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            return GAMER_E_CUDA;
+        if (want > 0 && want < per_sm) per_sm = want;
+        const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
+        kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh,
+                                                                status, partials, N, kc);
+        return cudaGetLastError() == cudaSuccess ? GAMER_OK : GAMER_E_CUDA;
+      }
+    }
     void (*kern)(const T*, T*, T*, const double*, const double*, uint32_t*, double*, int64_t,
-                 KConst<T, P>);
+                 KConst<T, P>, LevelGeom);
     if constexpr (MODE == GAMER_MODE_F64) {
-        kern = hydro_step_kernel<MODE, 1>;
-    } else if constexpr (MODE == GAMER_MODE_F32) {
-        kern = (minb == 2) ? hydro_step_kernel<MODE, 2>
-                           : (hydro_variant() == 1 ? hydro_step_kernel<MODE, 3, 1>
-                                                   : hydro_step_kernel<MODE, 3>);
+        kern = hydro_step_kernel<MODE, 1, 0, SRC>;
     } else {
-        kern = (minb == 2) ? hydro_step_kernel<MODE, 2> : hydro_step_kernel<MODE, 3>;
+        kern = (want == 2) ? hydro_step_kernel<MODE, 2, 0, SRC> : hydro_step_kernel<MODE, 3, 0, SRC>;
+        if constexpr (MODE == GAMER_MODE_F32 && SRC == 0) {
+            if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC>;
+        }
     }
     const int smem = int(sizeof(Smem<T>));
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -68,15 +103,33 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         return GAMER_E_CUDA;
     if (want > 0 && want < per_sm) per_sm = want;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
-    KConst<T, P> kc;
-    kc.gamma = T(p->gamma);
-    kc.gm1 = T(p->gamma - 1.0);
-    kc.gm1p = P(p->gamma - 1.0);
-    kc.limiter = p->limiter;
-    kc.pfb = p->predictor_fallback;
-    kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, static_cast<cudaStream_t>(stream)>>>(
-        in, out, face_flux, dt, dh, status, partials, N, kc);
+    kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh, status,
+                                                            partials, N, kc, geo);
     return cudaGetLastError() == cudaSuccess ? GAMER_OK : GAMER_E_CUDA;
+}
+
+template <int MODE>
+int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
+                  typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
+                  uint32_t* status, double* partials, int64_t N, const gh_params* p,
+                  void* stream) {
+    const LevelGeom geo = {1, 1, 1, 0};
+    return hydro_launch<MODE, 0>(in, out, face_flux, dt, dh, status, partials, N, p, geo,
+                                 stream);
+}
+
+template <int MODE>
+int hydro_advance_level(const typename Prec<MODE>::T* level, typename Prec<MODE>::T* out,
+                        typename Prec<MODE>::T* face_flux, int32_t gx, int32_t gy, int32_t gz,
+                        int32_t bc, const double* dt, const double* dh, uint32_t* status,
+                        double* partials, const gh_params* p, void* stream) {
+    if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1)) return GAMER_E_PARAM;
+    if (int64_t(gx) * 16 > (1 << 30) || int64_t(gy) * 16 > (1 << 30) ||
+        int64_t(gz) * 16 > (1 << 30))
+        return GAMER_E_PARAM;
+    const LevelGeom geo = {gx, gy, gz, bc};
+    return hydro_launch<MODE, 1>(level, out, face_flux, dt, dh, status, partials,
+                                 int64_t(gx) * gy * gz, p, geo, stream);
 }
 
 }  // namespace gamer

@@ -9,3 +9,12 @@ extern "C" int gamer_hydro_advance_mixed(const float* in, float* out, float* fac
     return gamer::hydro_advance<GAMER_MODE_MIXED>(in, out, face_flux, dt, dh, status, partials, N, p,
                                           stream);
 }
+
+extern "C" int gamer_hydro_advance_level_mixed(const float* level, float* out, float* face_flux,
+                                            int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                            const double* dt, const double* dh,
+                                            uint32_t* status, double* partials,
+                                            const gh_params* p, void* stream) {
+    return gamer::hydro_advance_level<GAMER_MODE_MIXED>(level, out, face_flux, gx, gy, gz, bc, dt, dh,
+                                                status, partials, p, stream);
+}

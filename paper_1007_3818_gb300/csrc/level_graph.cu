@@ -1,6 +1,7 @@
 // level_graph.cu -- one CUDA graph for the device-resident step of a uniform
 // level: ghost fill -> MUSCL-Hancock/Roe step -> dt / conservation reduction
-// (whose per-group dt feeds the next step).  A graph advances level_a into
+// (whose per-group dt feeds the next step); without a tiles buffer the ghost
+// fill is fused into the step kernel.  A graph advances level_a into
 // level_b; the caller alternates it with the graph of the swapped buffers, so
 // a run of steps needs no host involvement and no per-kernel launch overhead.
 #include <cuda_runtime.h>
@@ -32,6 +33,22 @@ int enqueue_step(int mode, const void* cur, void* nxt, void* tiles, void* ff, do
                  double* totals, void* ws, size_t ws_bytes, cudaStream_t s) {
     const int64_t G = int64_t(gx) * gy * gz;
     int rc;
+    if (!tiles) {  // fused ghost gather: one kernel reads the level directly
+        if (mode == GAMER_MODE_F32)
+            rc = gamer_hydro_advance_level_f32((const float*)cur, (float*)nxt, (float*)ff, gx, gy,
+                                               gz, bc, dt_group, dh_group, status, partials, p, s);
+        else if (mode == GAMER_MODE_MIXED)
+            rc = gamer_hydro_advance_level_mixed((const float*)cur, (float*)nxt, (float*)ff, gx,
+                                                 gy, gz, bc, dt_group, dh_group, status, partials,
+                                                 p, s);
+        else
+            rc = gamer_hydro_advance_level_f64((const double*)cur, (double*)nxt, (double*)ff, gx,
+                                               gy, gz, bc, dt_group, dh_group, status, partials,
+                                               p, s);
+        if (rc != GAMER_OK) return rc;
+        return gamer_hydro_dt(partials, G, nullptr, 1, dh_level, p->cfl, dt_level, totals,
+                              dt_group, ws, ws_bytes, s);
+    }
     if (mode == GAMER_MODE_F64)
         rc = gamer_fill_ghosts_uniform_f64((const double*)cur, (double*)tiles, gx, gy, gz, bc, s);
     else
@@ -67,8 +84,7 @@ extern "C" int gamer_level_graph_create(int32_t mode, void* level_a, void* level
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
     if (!(std::isfinite(p->cfl) && p->cfl > 0.0)) return GAMER_E_PARAM;
-    if (!level_a || !level_b || !tiles || !dt_group || !dh_group || !partials || !dh_level ||
-        !dt_level)
+    if (!level_a || !level_b || !dt_group || !dh_group || !partials || !dh_level || !dt_level)
         return GAMER_E_NULL;
     const DeviceInfo d = current_device();
     if (d.status != GAMER_OK) return d.status;

@@ -56,6 +56,11 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(gh_params), vp]
             f.restype = ctypes.c_int
+        for name in ("gamer_hydro_advance_level_f32", "gamer_hydro_advance_level_mixed",
+                     "gamer_hydro_advance_level_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, P(gh_params), vp]
+            f.restype = ctypes.c_int
         for name in ("gamer_fill_ghosts_uniform_f32", "gamer_fill_ghosts_uniform_f64"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, i32, i32, i32, i32, vp]
@@ -178,6 +183,50 @@ def gamer_hydro_advance_f64(inp, out, face_flux, dt, dh, status, partials, param
 
 def hydro_advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream=None):
     _advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream)
+
+
+_ADV_LEVEL = {GAMER_MODE_F32: "gamer_hydro_advance_level_f32",
+              GAMER_MODE_MIXED: "gamer_hydro_advance_level_mixed",
+              GAMER_MODE_F64: "gamer_hydro_advance_level_f64"}
+
+
+def hydro_advance_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status, partials,
+                        params, stream=None):
+    """One step of every group of a uniform level with the ghost gather fused
+    into the kernel: level/out [G,5,16,16,16] (G = gx*gy*gz), face_flux
+    [G,6,5,16,16] or None, dt/dh [G] f64, status [G] int32 or None, partials
+    [G,6] f64 or None."""
+    import torch
+    T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+    G = gx * gy * gz
+    for t, nm in ((level, "level"), (out, "out"), (face_flux, "face_flux"), (dt, "dt"),
+                  (dh, "dh"), (status, "status"), (partials, "partials")):
+        if t is not None and int(t.shape[0]) != G:
+            raise GamerError(-2, f"{nm} must hold gx*gy*gz = {G} groups")
+    args = [_ptr(level, T, (5, 16, 16, 16), "level"), _ptr(out, T, (5, 16, 16, 16), "out"),
+            _ptr(face_flux, T, (6, 5, 16, 16), "face_flux"), int(gx), int(gy), int(gz), int(bc),
+            _ptr(dt, torch.float64, (), "dt"), _ptr(dh, torch.float64, (), "dh"),
+            _ptr(status, torch.int32, (), "status"), _ptr(partials, torch.float64, (6,), "partials")]
+    rc = getattr(lib(), _ADV_LEVEL[mode])(*args, ctypes.byref(params), _stream(stream))
+    _check(rc, _ADV_LEVEL[mode])
+
+
+def gamer_hydro_advance_level_f32(level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                                  partials, params, stream=None):
+    hydro_advance_level(GAMER_MODE_F32, level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                        partials, params, stream)
+
+
+def gamer_hydro_advance_level_mixed(level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                                    partials, params, stream=None):
+    hydro_advance_level(GAMER_MODE_MIXED, level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                        partials, params, stream)
+
+
+def gamer_hydro_advance_level_f64(level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                                  partials, params, stream=None):
+    hydro_advance_level(GAMER_MODE_F64, level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
+                        partials, params, stream)
 
 
 def _fill(name, T, level, inp, gx, gy, gz, bc, stream):

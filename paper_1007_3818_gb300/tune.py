@@ -116,3 +116,28 @@ def _save(path, key, res):
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, default=str)
     os.replace(tmp, path)
+
+
+def tune_hydro_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status, partials,
+                     params, reps=5):
+    """As tune_hydro for gamer_hydro_advance_level_<mode> (fused ghost gather);
+    the level kernel comes in the one-problem-at-a-time shape only."""
+    import torch
+    key = ("level", torch.cuda.get_device_name(), int(mode), _bucket(gx * gy * gz))
+    if key in _cache:
+        native.gamer_set_hydro_ctas_per_sm(mode, _cache[key]["ctas_per_sm"])
+        native.gamer_set_hydro_variant(0)
+        return _cache[key]
+    candidates = [1] if mode == native.GAMER_MODE_F64 else [2, 3]
+    native.gamer_set_hydro_variant(0)
+    results = {}
+    for c in candidates:
+        native.gamer_set_hydro_ctas_per_sm(mode, c)
+        results[c] = _time(lambda: native.hydro_advance_level(
+            mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status, partials, params), reps)
+    best = min(results, key=results.get)
+    native.gamer_set_hydro_ctas_per_sm(mode, best)
+    res = {"ctas_per_sm": best, "variant": 0, "ms": results[best],
+           "all": {str(c): t for c, t in results.items()}}
+    _cache[key] = res
+    return res

@@ -268,3 +268,119 @@ def test_sod_single_group_ten_steps(mode):
     assert rel_l1_fields(got[-1], ref[-1]) <= tol
     # transverse momenta stay exactly zero
     assert not got[-1][:, 2].any() and not got[-1][:, 3].any()
+
+
+# --------------------------------------------------------------------------
+# Every code-shape variant of the kernel (what the autotuner may pick) must
+# meet the same parity bar.
+VARIANTS = [pytest.param(F32, 0, id="f32-v0"), pytest.param(F32, 1, id="f32-v1"),
+            pytest.param(F32, 2, id="f32-v2"), pytest.param(MIXED, 2, id="mixed-v2"),
+            pytest.param(F64, 2, id="f64-v2")]
+
+
+@pytest.fixture
+def variant_guard():
+    from paper_1007_3818_gb300 import native
+    yield native
+    native.gamer_set_hydro_variant(0)
+    for m in (F32, MIXED, F64):
+        native.gamer_set_hydro_ctas_per_sm(m, 0)
+
+
+@pytest.mark.parametrize("mode,variant", VARIANTS)
+def test_variant_parity(variant_guard, mode, variant):
+    native = variant_guard
+    native.gamer_set_hydro_variant(variant)
+    tol = TOL_F64 if mode == F64 else TOL_F32_1
+    g = 5 / 3
+    # smooth groups, more than one wave of groups per CTA
+    compare_step(wl.random_smooth_groups(9, seed=77, gamma=g), 2e-3, 1 / 256, g, mode, tol)
+    # per-group dt / dh
+    tiles, level, dh_level = wl.amr_batch(counts=(2, 3, 4), seed=8, base_n=64)
+    compare_step(tiles, 0.3 * dh_level[level] / 4.0, dh_level[level], g, mode, tol)
+    # other limiters (runtime-limiter builds)
+    for lim in (1, 2):
+        compare_step(wl.random_smooth_groups(2, seed=5, gamma=g), 2e-3, 1 / 256, g, mode, tol,
+                     limiter=lim)
+    # both fallbacks (status compared exactly in FP64)
+    stress = wl.stress_groups(3, seed=11, gamma=1.4)
+    if mode == F64:
+        compare_step(stress, 0.004, 1 / 16, 1.4, mode, tol)
+    else:
+        host = host_input(stress, mode)
+        out, _, st, _ = gpu_advance(host, 0.004, 1 / 16, 1.4, mode)
+        r_out, _, r_st, _ = oracle.advance_groups(host, 0.004, 1 / 16, gamma=1.4)
+        assert ((st & 3) == (r_st & 3)).all()
+        assert rel_l1_fields(out, r_out) <= 1e-3
+
+
+@pytest.mark.parametrize("mode,variant", VARIANTS)
+def test_variant_uniform_state_bitwise(variant_guard, mode, variant):
+    native = variant_guard
+    native.gamer_set_hydro_variant(variant)
+    g = 5 / 3
+    U = oracle.cons(np.array([1.7, 0.4, -1.3, 0.25, 0.6]), g)
+    if mode != F64:
+        U = U.astype(np.float32).astype(np.float64)
+    tiles = np.broadcast_to(U[None, :, None, None, None], (2, 5, 20, 20, 20)).copy()
+    out, ff, st, _ = gpu_advance(tiles, 1e-2, 1 / 64, g, mode)
+    assert np.array_equal(out, tiles[:, :, 2:18, 2:18, 2:18]) and (st == 0).all()
+
+
+# --------------------------------------------------------------------------
+# Fused ghost gather: the level read directly by the step kernel
+@pytest.mark.parametrize("mode", [F32, MIXED, F64], ids=["f32", "mixed", "f64"])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1), (1, 3, 2), (4, 1, 1)])
+def test_fused_level_step_equals_fill_then_step(mode, bc, dims):
+    import torch
+    from paper_1007_3818_gb300 import native
+    gx, gy, gz = dims
+    G = gx * gy * gz
+    g = 5 / 3
+    rng = np.random.default_rng(G * 7 + bc)
+    # a smooth positive state, one group per 16^3 block
+    U = wl.fourier_level(n=16, seed=int(rng.integers(1 << 30)), gamma=g)
+    lv = np.concatenate([wl.level_to_groups(
+        wl.fourier_level(n=16, seed=int(rng.integers(1 << 30)), gamma=g)) for _ in range(G)])
+    T = torch_dtype(mode)
+    if mode != F64:
+        lv = lv.astype(np.float32).astype(np.float64)
+    d_lv = torch.from_numpy(lv).to("cuda", T)
+    dt = torch.full((G,), 2e-3, device="cuda", dtype=torch.float64)
+    dh = torch.full((G,), 1 / 64, device="cuda", dtype=torch.float64)
+    params = native.make_params(g)
+
+    def run(fused):
+        out = torch.full((G, 5, 16, 16, 16), float("nan"), device="cuda", dtype=T)
+        ff = torch.full((G, 6, 5, 16, 16), float("nan"), device="cuda", dtype=T)
+        st = torch.full((G,), -1, device="cuda", dtype=torch.int32)
+        part = torch.full((G, 6), float("nan"), device="cuda", dtype=torch.float64)
+        if fused:
+            native.hydro_advance_level(mode, d_lv, out, ff, gx, gy, gz, bc, dt, dh, st, part,
+                                       params)
+        else:
+            tiles = torch.empty((G, 5, 20, 20, 20), device="cuda", dtype=T)
+            fill = (native.gamer_fill_ghosts_uniform_f64 if mode == F64
+                    else native.gamer_fill_ghosts_uniform_f32)
+            fill(d_lv, tiles, gx, gy, gz, bc)
+            native.hydro_advance(mode, tiles, out, ff, dt, dh, st, part, params)
+        torch.cuda.synchronize()
+        return [t.cpu().numpy() for t in (out, ff, st, part)]
+
+    a, b = run(True), run(False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    tiles = oracle.fill_ghosts_uniform(lv, gx, gy, gz, bc)
+    r_out, _, r_st, _ = oracle.advance_groups(tiles, 2e-3, 1 / 64, gamma=g)
+    assert rel_l1_fields(a[0].astype(np.float64), r_out) <= (TOL_F64 if mode == F64 else TOL_F32_1)
+
+
+def test_fused_level_rejects_in_place_update():
+    import torch
+    from paper_1007_3818_gb300 import native
+    lv = torch.zeros((8, 5, 16, 16, 16), device="cuda")
+    d = torch.ones(8, device="cuda", dtype=torch.float64)
+    with pytest.raises(native.GamerError):
+        native.hydro_advance_level(F32, lv, lv, None, 2, 2, 2, 0, d, d, None, None,
+                                   native.make_params(1.4))
