@@ -48,14 +48,14 @@ template <> struct Prec<GAMER_MODE_F32> { using T = float; using P = float; };
 template <> struct Prec<GAMER_MODE_MIXED> { using T = float; using P = double; };
 template <> struct Prec<GAMER_MODE_F64> { using T = double; using P = double; };
 
-template <class T>
+template <class T, int RING = 2>
 struct alignas(16) Smem {
-    T raw[2][5 * kPlane];  // TMA ring of conserved input planes
+    T raw[RING][5 * kPlane];  // ring of conserved input planes (TMA / cp.async)
     T W[3][5 * kPlane];    // primitive planes
     T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
     T fxy[5 * kFluxStride];  // x- and y-face fluxes of the current plane
     double red[kThreads / 32][6];
-    uint64_t mbar[2];
+    uint64_t mbar[RING];
     uint32_t status;
 };
 
@@ -516,9 +516,9 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
 
 // Copies input plane kp into its ring slot of any shared layout with raw[2][]
 // and mbar[2] members.
-template <class SM, class T>
+template <int RING = 2, class SM, class T>
 __device__ __forceinline__ void issue_plane(SM& S, const T* gin, int kp) {
-    const int slot = (kp + 2) & 1;
+    const int slot = (kp + 2) % RING;
     constexpr uint32_t bytes = 5u * kPlane * sizeof(T);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive_expect_tx(&S.mbar[slot], bytes);
@@ -548,11 +548,11 @@ __device__ __forceinline__ int wrap_coord(int X, int n, int bc) {
 // group's 16 interior cells and the two x-ghost pairs of its neighbours -- in
 // 2-cell cp.async copies (single cells where a clamped boundary repeats one);
 // every thread then arrives on the slot's barrier (expected count kThreads).
-template <class SM, class T>
+template <int RING, class SM, class T>
 __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
                                              const LevelGeom& L, int bx, int by, int bz,
                                              int kp) {
-    const int slot = (kp + 2) & 1;
+    const int slot = (kp + 2) % RING;
     const int r = threadIdx.x;
     if (r < 100) {
         constexpr int PAIR = 2 * int(sizeof(T)), ONE = int(sizeof(T));
@@ -590,20 +590,20 @@ __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
 
 // Plane loaders by input kind (struct dispatch): 0 -- TMA bulk copies of the
 // tile's plane issued by thread 0; 1 -- gather from the level by 100 threads.
-template <int SRC> struct PlaneLoader;
-template <> struct PlaneLoader<0> {
+template <int SRC, int RING> struct PlaneLoader;
+template <int RING> struct PlaneLoader<0, RING> {
     template <class SM, class T>
     static __device__ __forceinline__ void load(SM& S, const T* gin, const T*, const LevelGeom&,
                                                 int, int, int, int kp) {
-        if (threadIdx.x == 0) issue_plane(S, gin, kp);
+        if (threadIdx.x == 0) issue_plane<RING>(S, gin, kp);
     }
 };
-template <> struct PlaneLoader<1> {
+template <int RING> struct PlaneLoader<1, RING> {
     template <class SM, class T>
     static __device__ __forceinline__ void load(SM& S, const T*, const T* level,
                                                 const LevelGeom& L, int bx, int by, int bz,
                                                 int kp) {
-        gather_plane(S, level, L, bx, by, bz, kp);
+        gather_plane<RING>(S, level, L, bx, by, bz, kp);
     }
 };
 
@@ -634,7 +634,9 @@ template <> struct SumAcc<float> {
 // SRC 0: `in` holds N ghost-padded 20^3 tiles, loaded plane by plane with the
 // TMA engine; SRC 1: `in` is the uniform level `geo` (N = gx*gy*gz groups) and
 // each plane is gathered from the group and its neighbours (fused ghost fill).
-template <int MODE, int MINB, int OOL = 0, int SRC = 0>
+// RING: input planes in flight (2: the copy of plane k+2 goes out after phase A
+// of plane k; 3: plane k+3 does, one full iteration ahead of its use).
+template <int MODE, int MINB, int OOL = 0, int SRC = 0, int RING = 2>
 __global__ void __launch_bounds__(kThreads, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
@@ -645,12 +647,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
                       LevelGeom geo) {
     using T = typename Prec<MODE>::T;
     extern __shared__ __align__(128) unsigned char smem_bytes[];
-    Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_bytes);
+    Smem<T, RING>& S = *reinterpret_cast<Smem<T, RING>*>(smem_bytes);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], SRC == 0 ? 1 : kThreads);
+        for (int s = 0; s < RING; ++s) mbar_init(&S.mbar[s], SRC == 0 ? 1 : kThreads);
         mbar_init_fence();
     }
     __syncthreads();
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                   gbz = int(g / (int64_t(geo.gx) * geo.gy));
         // one input plane into its ring slot (all threads call this)
         auto load_plane = [&](int kp) {
-            PlaneLoader<SRC>::load(S, gin, in, geo, gbx, gby, gbz, kp);
+            PlaneLoader<SRC, RING>::load(S, gin, in, geo, gbx, gby, gbz, kp);
         };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * 7680 : nullptr;
@@ -703,11 +705,14 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0))
                 st |= GAMER_ST_BAD_INPUT;
         }
+        // prologue: planes -2, -1, 0 -> primitives (W slots 0, 1, 2).  With two
+        // ring slots plane 0 reuses the slot of plane -2; with three, plane 1
+        // goes into it, so that it is in flight before the first iteration.
+        bool timed_out = false;
         load_plane(-2);
         load_plane(-1);
-        pending |= 3u;
-        // prologue: planes -2, -1, 0 -> primitives; plane 0 reuses slot 0
-        bool timed_out = false;
+        if (RING == 3) load_plane(0);
+        pending |= (RING == 3) ? 7u : 3u;
         if (mbar_wait(&S.mbar[0], parity & 1u)) {
             parity ^= 1u;
             pending &= ~1u;
@@ -716,13 +721,14 @@ __global__ void __launch_bounds__(kThreads, MINB)
             timed_out = true;
         }
         if (__syncthreads_or(timed_out)) goto abort_group;
-        load_plane(0);
+        load_plane(RING == 3 ? 1 : 0);
         pending |= 1u;
-        for (int s = 1; s >= 0; --s) {  // plane -1 (slot 1), then plane 0 (slot 0)
+        for (int kp = -1; kp <= 0; ++kp) {
+            const int s = (kp + 2) % RING;
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
-                convert_plane<MODE>(S.raw[s], S.W[(s == 1) ? 1 : 2], (s == 1) ? -1 : 0, kc, st);
+                convert_plane<MODE>(S.raw[s], S.W[kp + 2], kp, kc, st);
             } else {
                 timed_out = true;
             }
@@ -753,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 const T* Wm = S.W[(k + 1) % 3];
                 const T* W0 = S.W[(k + 2) % 3];
                 const T* Wp = S.W[(k + 3) % 3];
-                const T* Uk = S.raw[(k + 2) & 1];
+                const T* Uk = S.raw[(k + 2) % RING];
                 const bool inner = (k >= 0 && k <= 15);
 
                 // ---- phase CA, part C(k-1): finish plane k-2, set up plane k-1
@@ -855,10 +861,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     }
                 }
                 __syncthreads();
-                // plane k has been read: its slot takes plane k+2
-                if (k <= 15) {
-                    load_plane(k + 2);
-                    pending |= 1u << ((k + 2) & 1);
+                // plane k has been read: its slot takes plane k + RING
+                if (k + RING <= 17) {
+                    load_plane(k + RING);
+                    pending |= 1u << ((k + 2) % RING);
                 }
 
                 // ---- phase B(k): Riemann solves
@@ -951,7 +957,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 }
                 // plane k+2 -> primitives (into the slot of plane k-1)
                 if (k <= 15) {
-                    const int slot = (k + 2) & 1;
+                    const int slot = (k + 4) % RING;
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
@@ -1003,7 +1009,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         // still in flight so none lands after the CTA exits, flag the group and
         // stop this CTA.
         if (tid == 0) {
-            for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < RING; ++s)
                 if (pending & (1u << s)) mbar_wait(&S.mbar[s], (parity >> s) & 1u);
             if (status) status[g] = GAMER_ST_INTERNAL_TIMEOUT;
         }

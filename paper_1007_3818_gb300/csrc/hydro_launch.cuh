@@ -82,17 +82,25 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         return cudaGetLastError() == cudaSuccess ? GAMER_OK : GAMER_E_CUDA;
       }
     }
+    // builds with room to spare in shared memory (2 CTAs/SM in FP32, FP64)
+    // keep three input planes in flight instead of two
     void (*kern)(const T*, T*, T*, const double*, const double*, uint32_t*, double*, int64_t,
                  KConst<T, P>, LevelGeom);
+    int smem = int(sizeof(Smem<T, 2>));
     if constexpr (MODE == GAMER_MODE_F64) {
-        kern = hydro_step_kernel<MODE, 1, 0, SRC>;
+        kern = hydro_step_kernel<MODE, 1, 0, SRC, 3>;
+        smem = int(sizeof(Smem<T, 3>));
     } else {
-        kern = (want == 2) ? hydro_step_kernel<MODE, 2, 0, SRC> : hydro_step_kernel<MODE, 3, 0, SRC>;
+        if (want == 2) {
+            kern = hydro_step_kernel<MODE, 2, 0, SRC, 3>;
+            smem = int(sizeof(Smem<T, 3>));
+        } else {
+            kern = hydro_step_kernel<MODE, 3, 0, SRC, 2>;
+        }
         if constexpr (MODE == GAMER_MODE_F32 && SRC == 0) {
-            if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC>;
+            if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
         }
     }
-    const int smem = int(sizeof(Smem<T>));
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return GAMER_E_CUDA;
