@@ -119,6 +119,9 @@ int gamer_hydro_advance_f64(const double* in, double* out, double* face_flux, co
  *   out, face_flux, dt, dh, status, partials: as gamer_hydro_advance_* with
  *             N = G.
  *   bc        0 periodic, 1 zero-gradient.
+ * Returns GAMER_E_PARAM for negative extents, bc not 0 or 1, an extent above
+ * 2^26 groups, or more than (2^31 - 2048) / 1280 (about 1.68 million) groups
+ * in one z-layer (gx*gy).
  * Results equal gamer_fill_ghosts_uniform_* followed by gamer_hydro_advance_*
  * bit for bit.
  */

@@ -54,6 +54,13 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
                  : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared cached in L2 only (the data of a
+// patch group is read once per SM); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+
 // Arrival of this thread on `bar` once all its earlier cp.async copies have
 // landed (counts as one of the barrier's expected arrivals).
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {

@@ -50,7 +50,7 @@ template <> struct Prec<GAMER_MODE_F64> { using T = double; using P = double; };
 
 template <class T, int RING = 2>
 struct alignas(16) Smem {
-    T raw[RING][5 * kPlane];  // ring of conserved input planes (TMA / cp.async)
+    T raw[RING][5 * kPlane + 4];  // ring of conserved input planes (TMA / cp.async)
     T W[3][5 * kPlane];    // primitive planes
     T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
     T fxy[5 * kFluxStride];  // x- and y-face fluxes of the current plane
@@ -535,75 +535,160 @@ struct LevelGeom {
     int gx, gy, gz, bc;
 };
 
-__device__ __forceinline__ int wrap_coord(int X, int n, int bc) {
-    if (bc == 0) {
-        X %= n;
-        return X < 0 ? X + n : X;
-    }
-    return X < 0 ? 0 : (X >= n ? n - 1 : X);
+// Level coordinate X, at most two cells outside [0, n), mapped into the level:
+// periodic wrap (bc 0) or zero-gradient clamp (bc 1).
+__device__ __forceinline__ int wrap_near(int X, int n, int bc) {
+    if (X < 0) return bc == 0 ? X + n : 0;
+    if (X >= n) return bc == 0 ? X - n : n - 1;
+    return X;
 }
 
-// Builds input plane kp of group (bx, by, bz) in its ring slot straight from
-// the level: thread r < 100 copies row (v, j) = (r / 20, r % 20) -- the
-// group's 16 interior cells and the two x-ghost pairs of its neighbours -- in
-// 2-cell cp.async copies (single cells where a clamped boundary repeats one);
-// every thread then arrives on the slot's barrier (expected count kThreads).
+// Element offset of the input plane inside its ring slot.  The fused gather
+// moves FP32 planes 8 bytes in, so that the 16 interior cells of every row
+// (tile columns 2..17) start on a 16-byte boundary.
+template <int SRC, class T>
+__device__ __forceinline__ constexpr int raw_offset() {
+    return (SRC == 1 && sizeof(T) == 4) ? 2 : 0;
+}
+
+// distance of tile coordinate c in [0, 20) from the interior [2, 18)
+__device__ __forceinline__ int ghost_depth(int c) { return c < 2 ? 2 - c : (c > 17 ? c - 17 : 0); }
+
+// The fused gather copies, for input plane kp of a group, every cell the
+// stencil reads (is_read_cell) and no more:
+//  * interior runs: the 16 cells x in [0, 16) of tile row j, for the rows
+//    with depth(j) + depth(kp) <= 2, in 16-byte copies; thread t takes chunk
+//    t % CH of row (t / CH) % 20 for variables v0, v0 + VS, ... (consecutive
+//    lanes read consecutive 16 bytes of a level row; rows land 80 or 160
+//    bytes apart in shared memory, which spreads a warp over all banks);
+//  * x ghosts: the two cells on each side of rows j = 1..18 of planes with
+//    depth(kp) <= 1 (180 items, one 2-cell copy each; single cells where a
+//    clamped boundary repeats one): thread t takes items t and t + 160.
+// Everything but the z offset is fixed for a group and worked out once into
+// a per-thread plan kept in shared memory (registers are the kernel's
+// scarcest resource): level offsets relative to the z-layer of groups, in
+// units of 16 cells (32 bits for up to 2^31 / 1280 groups per layer), and
+// the ghost items' shared-memory destinations.
+struct alignas(16) GatherPlan {
+    int32_t chunk;  // 16-cell offset of the thread's interior row (variable v0)
+    int32_t gh[2];  // 16-cell offsets of the rows of its x-ghost items
+    uint32_t bits;  // [0,4), [4,8): x of ghost item 0, 1 inside its 16-cell row;
+                    // 8, 9: item is a 2-cell copy; [10,21), [21,32): item 0, 1
+                    // offset in the plane
+};
+
+// row and 16-byte chunk of the interior run of this thread
+template <class T> struct GatherRow {
+    static constexpr int E16 = 16 / int(sizeof(T));  // cells per 16-byte chunk
+    static constexpr int CH = 16 / E16;              // chunks per 16-cell row: 4 or 8
+    static constexpr int VS = kThreads / CH / 20;    // variables per pass: 2 or 1
+    static_assert(VS * 20 * CH == kThreads, "gather mapping");
+    int q, v0, j;
+    __device__ __forceinline__ GatherRow() {
+        const int R0 = int(threadIdx.x) / CH;
+        q = int(threadIdx.x) - R0 * CH;
+        v0 = R0 / 20;
+        j = R0 - 20 * v0;
+    }
+};
+
+template <class T>
+__device__ __forceinline__ GatherPlan make_plan(const LevelGeom& L, int bx, int by) {
+    const GatherRow<T> w;
+    GatherPlan P;
+    const int ny = 16 * L.gy, nx = 16 * L.gx;
+    const int Y = wrap_near(by * 16 + w.j - 2, ny, L.bc);
+    P.chunk = ((Y >> 4) * L.gx + bx) * 1280 + w.v0 * 256 + (Y & 15);
+    P.bits = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        P.gh[r] = 0;
+        const int it = int(threadIdx.x) + r * kThreads;
+        if (it < 180) {
+            const int v = it / 36, rem = it - 36 * v;
+            const int jj = 1 + (rem >> 1), side = rem & 1;
+            const int Yg = wrap_near(by * 16 + jj - 2, ny, L.bc);
+            const int X0 = wrap_near(side ? bx * 16 + 16 : bx * 16 - 2, nx, L.bc);
+            const int X1 = wrap_near(side ? bx * 16 + 17 : bx * 16 - 1, nx, L.bc);
+            P.gh[r] = ((Yg >> 4) * L.gx + (X0 >> 4)) * 1280 + v * 256 + (Yg & 15);
+            P.bits |= uint32_t(X0 & 15) << (4 * r);
+            if (X1 == X0 + 1) P.bits |= 1u << (8 + r);
+            P.bits |= uint32_t(v * kPlane + jj * 20 + (side ? 18 : 0)) << (10 + 11 * r);
+        }
+    }
+    return P;
+}
+
+// Gathers input plane kp of the group of plan P (z index bz) from the level
+// into its ring slot; every thread then arrives on the slot's barrier
+// (expected count kThreads).
 template <int RING, class SM, class T>
 __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
-                                             const LevelGeom& L, int bx, int by, int bz,
+                                             const LevelGeom& L, const GatherPlan& P, int bz,
                                              int kp) {
+    using G = GatherRow<T>;
+    const G w;
     const int slot = (kp + 2) % RING;
-    const int r = threadIdx.x;
-    if (r < 100) {
-        constexpr int PAIR = 2 * int(sizeof(T)), ONE = int(sizeof(T));
-        const int v = r / 20, j = r - v * 20;
-        const int nx = 16 * L.gx;
-        const int Z = wrap_coord(bz * 16 + kp, 16 * L.gz, L.bc);
-        const int Y = wrap_coord(by * 16 + j - 2, 16 * L.gy, L.bc);
-        const T* row = level + ((int64_t(Z >> 4) * L.gy + (Y >> 4)) * L.gx) * 20480 +
-                       v * 4096 + (Z & 15) * 256 + (Y & 15) * 16;
-        T* dst = &S.raw[slot][v * kPlane + j * 20];
-        const T* own = row + int64_t(bx) * 20480;
+    T* plane = S.raw[slot] + raw_offset<1, T>();
+    const int Z = wrap_near(bz * 16 + kp, 16 * L.gz, L.bc);
+    const T* lz = level + int64_t(Z >> 4) * (L.gy * L.gx) * 20480 + (Z & 15) * 256;
+    const int dk = ghost_depth(kp + 2);
+    if (ghost_depth(w.j) + dk <= 2) {
+        const T* src = lz + int64_t(P.chunk) * 16 + w.q * G::E16;
+        T* dst = plane + w.v0 * kPlane + w.j * 20 + 2 + w.q * G::E16;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) cp_async<PAIR>(dst + 2 + 2 * c, own + 2 * c);
-        const int xl0 = wrap_coord(bx * 16 - 2, nx, L.bc), xl1 = wrap_coord(bx * 16 - 1, nx, L.bc);
-        const int xr0 = wrap_coord(bx * 16 + 16, nx, L.bc), xr1 = wrap_coord(bx * 16 + 17, nx, L.bc);
-        const T* sl0 = row + int64_t(xl0 >> 4) * 20480 + (xl0 & 15);
-        const T* sl1 = row + int64_t(xl1 >> 4) * 20480 + (xl1 & 15);
-        const T* sr0 = row + int64_t(xr0 >> 4) * 20480 + (xr0 & 15);
-        const T* sr1 = row + int64_t(xr1 >> 4) * 20480 + (xr1 & 15);
-        if (xl1 == xl0 + 1) {
-            cp_async<PAIR>(dst, sl0);
-        } else {
-            cp_async<ONE>(dst, sl0);
-            cp_async<ONE>(dst + 1, sl1);
+        for (int v = 0; v < 5; v += G::VS) {
+            if (v + w.v0 < 5) cp_async_cg16(dst, src);
+            dst += G::VS * kPlane;
+            src += G::VS * 4096;
         }
-        if (xr1 == xr0 + 1) {
-            cp_async<PAIR>(dst + 18, sr0);
-        } else {
-            cp_async<ONE>(dst + 18, sr0);
-            cp_async<ONE>(dst + 19, sr1);
+    }
+    if (dk <= 1) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (r == 1 && threadIdx.x >= 180 - kThreads) break;
+            const T* src = lz + int64_t(P.gh[r]) * 16 + ((P.bits >> (4 * r)) & 15u);
+            T* dst = plane + ((P.bits >> (10 + 11 * r)) & 2047u);
+            if (P.bits & (1u << (8 + r))) {
+                cp_async<2 * int(sizeof(T))>(dst, src);
+            } else {
+                cp_async<int(sizeof(T))>(dst, src);
+                cp_async<int(sizeof(T))>(dst + 1, src);
+            }
         }
     }
     cp_async_arrive(&S.mbar[slot]);
 }
 
-// Plane loaders by input kind (struct dispatch): 0 -- TMA bulk copies of the
-// tile's plane issued by thread 0; 1 -- gather from the level by 100 threads.
-template <int SRC, int RING> struct PlaneLoader;
-template <int RING> struct PlaneLoader<0, RING> {
-    template <class SM, class T>
-    static __device__ __forceinline__ void load(SM& S, const T* gin, const T*, const LevelGeom&,
-                                                int, int, int, int kp) {
+// Plane loaders by input kind, set up once per group: 0 -- TMA bulk copies of
+// the tile's plane issued by thread 0; 1 -- gather from the level by all
+// threads, with the plan in `plan` (kThreads entries of shared memory).
+template <int SRC, int RING, class T> struct PlaneLoader;
+template <int RING, class T> struct PlaneLoader<0, RING, T> {
+    static constexpr size_t kExtraSmem = 0;
+    const T* gin;
+    __device__ __forceinline__ PlaneLoader(const T* in, int64_t g, const LevelGeom&, GatherPlan*)
+        : gin(in + g * 40000) {}
+    template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {
         if (threadIdx.x == 0) issue_plane<RING>(S, gin, kp);
     }
 };
-template <int RING> struct PlaneLoader<1, RING> {
-    template <class SM, class T>
-    static __device__ __forceinline__ void load(SM& S, const T*, const T* level,
-                                                const LevelGeom& L, int bx, int by, int bz,
-                                                int kp) {
-        gather_plane<RING>(S, level, L, bx, by, bz, kp);
+template <int RING, class T> struct PlaneLoader<1, RING, T> {
+    static constexpr size_t kExtraSmem = kThreads * sizeof(GatherPlan);
+    const T* level;
+    const LevelGeom& L;
+    GatherPlan* plan;
+    int bz;
+    __device__ __forceinline__ PlaneLoader(const T* in, int64_t g, const LevelGeom& geo,
+                                           GatherPlan* plan_)
+        : level(in), L(geo), plan(plan_ + threadIdx.x) {
+        const int bx = int(g % geo.gx), by = int((g / geo.gx) % geo.gy);
+        bz = int(g / (int64_t(geo.gx) * geo.gy));
+        *plan = make_plan<T>(geo, bx, by);  // read back by this thread only
+    }
+    template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {
+        const GatherPlan P = *plan;
+        gather_plane<RING>(S, level, L, P, bz, kp);
     }
 };
 
@@ -648,6 +733,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
     using T = typename Prec<MODE>::T;
     extern __shared__ __align__(128) unsigned char smem_bytes[];
     Smem<T, RING>& S = *reinterpret_cast<Smem<T, RING>*>(smem_bytes);
+    constexpr int ROFF = raw_offset<SRC, T>();
+    GatherPlan* gplan = reinterpret_cast<GatherPlan*>(smem_bytes + sizeof(Smem<T, RING>));
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
@@ -687,13 +774,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const T igm1 = T(1) / kc.gm1;
 
     for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
-        const T* gin = in + g * 40000;
-        const int gbx = int(g % geo.gx), gby = int((g / geo.gx) % geo.gy),
-                  gbz = int(g / (int64_t(geo.gx) * geo.gy));
-        // one input plane into its ring slot (all threads call this)
-        auto load_plane = [&](int kp) {
-            PlaneLoader<SRC, RING>::load(S, gin, in, geo, gbx, gby, gbz, kp);
-        };
+        // one input plane into its ring slot (all threads call load_plane)
+        const PlaneLoader<SRC, RING, T> loader(in, g, geo, gplan);
+        auto load_plane = [&](int kp) { loader.load(S, kp); };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * 7680 : nullptr;
         const double dtg = dt[g], dhg = dh[g];
@@ -716,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (mbar_wait(&S.mbar[0], parity & 1u)) {
             parity ^= 1u;
             pending &= ~1u;
-            convert_plane<MODE>(S.raw[0], S.W[0], -2, kc, st);
+            convert_plane<MODE>(S.raw[0] + ROFF, S.W[0], -2, kc, st);
         } else {
             timed_out = true;
         }
@@ -728,7 +811,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
-                convert_plane<MODE>(S.raw[s], S.W[kp + 2], kp, kc, st);
+                convert_plane<MODE>(S.raw[s] + ROFF, S.W[kp + 2], kp, kc, st);
             } else {
                 timed_out = true;
             }
@@ -759,7 +842,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 const T* Wm = S.W[(k + 1) % 3];
                 const T* W0 = S.W[(k + 2) % 3];
                 const T* Wp = S.W[(k + 3) % 3];
-                const T* Uk = S.raw[(k + 2) % RING];
+                const T* Uk = S.raw[(k + 2) % RING] + ROFF;
                 const bool inner = (k >= 0 && k <= 15);
 
                 // ---- phase CA, part C(k-1): finish plane k-2, set up plane k-1
@@ -961,7 +1044,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
-                        convert_plane<MODE>(S.raw[slot], S.W[(k + 4) % 3], k + 2, kc, st);
+                        convert_plane<MODE>(S.raw[slot] + ROFF, S.W[(k + 4) % 3], k + 2, kc, st);
                     } else {
                         timed_out = true;
                     }

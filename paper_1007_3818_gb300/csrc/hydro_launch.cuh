@@ -86,14 +86,16 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     // keep three input planes in flight instead of two
     void (*kern)(const T*, T*, T*, const double*, const double*, uint32_t*, double*, int64_t,
                  KConst<T, P>, LevelGeom);
-    int smem = int(sizeof(Smem<T, 2>));
+    // (the fused gather adds its per-thread plans after the Smem block)
+    constexpr int extra = int(PlaneLoader<SRC, 2, T>::kExtraSmem);
+    int smem = int(sizeof(Smem<T, 2>)) + extra;
     if constexpr (MODE == GAMER_MODE_F64) {
         kern = hydro_step_kernel<MODE, 1, 0, SRC, 3>;
-        smem = int(sizeof(Smem<T, 3>));
+        smem = int(sizeof(Smem<T, 3>)) + extra;
     } else {
         if (want == 2) {
             kern = hydro_step_kernel<MODE, 2, 0, SRC, 3>;
-            smem = int(sizeof(Smem<T, 3>));
+            smem = int(sizeof(Smem<T, 3>)) + extra;
         } else {
             kern = hydro_step_kernel<MODE, 3, 0, SRC, 2>;
         }
@@ -135,6 +137,9 @@ int hydro_advance_level(const typename Prec<MODE>::T* level, typename Prec<MODE>
     if (int64_t(gx) * 16 > (1 << 30) || int64_t(gy) * 16 > (1 << 30) ||
         int64_t(gz) * 16 > (1 << 30))
         return GAMER_E_PARAM;
+    // the gather's per-group plan holds level offsets within a z-layer of
+    // groups in units of 16 cells as 32-bit integers
+    if (int64_t(gx) * gy * 1280 + 2048 > INT32_MAX) return GAMER_E_PARAM;
     const LevelGeom geo = {gx, gy, gz, bc};
     return hydro_launch<MODE, 1>(level, out, face_flux, dt, dh, status, partials,
                                  int64_t(gx) * gy * gz, p, geo, stream);

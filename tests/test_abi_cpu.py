@@ -89,6 +89,27 @@ def test_advance_rejects_bad_arguments(lib, name):
              None, None, 4, None, None) == -1            # params NULL
 
 
+@pytest.mark.parametrize("name", ["gamer_hydro_advance_level_f32",
+                                  "gamer_hydro_advance_level_mixed",
+                                  "gamer_hydro_advance_level_f64"])
+def test_advance_level_rejects_bad_arguments(lib, name):
+    f = getattr(lib, name)
+    prm = native.make_params(1.4)
+
+    def call(level=FAKE, out=FAKE + (1 << 32), gx=2, gy=2, gz=2, bc=0, dt=FAKE + (2 << 32)):
+        return f(P(level) if level else None, P(out), None, gx, gy, gz, bc, P(dt),
+                 P(FAKE + (3 << 32)), None, None, ctypes.byref(prm), None)
+
+    assert call(bc=2) == -2
+    assert call(gx=-1) == -2
+    assert call(gz=1 << 27) == -2                     # extent above 2^26 groups
+    assert call(gx=1300, gy=1300, gz=1) == -2         # z-layer beyond the gather's offsets
+    assert call(gx=0) == 0                            # empty level
+    assert call(level=None) == -1
+    assert call(level=FAKE + 8) == -3                 # level needs 16 B alignment
+    assert call(out=FAKE + 4096) == -6                # out inside the level
+
+
 def test_fill_ghosts_rejects_bad_arguments(lib):
     f = lib.gamer_fill_ghosts_uniform_f32
     assert f(P(FAKE), P(FAKE + (1 << 30)), 2, 2, 2, 2, None) == -2     # bc

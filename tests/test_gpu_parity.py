@@ -333,6 +333,21 @@ def test_variant_uniform_state_bitwise(variant_guard, mode, variant):
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1), (1, 3, 2), (4, 1, 1)])
 def test_fused_level_step_equals_fill_then_step(mode, bc, dims):
+    _fused_vs_fill(mode, bc, dims)
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED], ids=["f32", "mixed"])
+@pytest.mark.parametrize("ctas", [2, 3])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1)])
+def test_fused_level_launch_shapes(variant_guard, mode, ctas, bc, dims):
+    """Both register/shared-memory builds (2 CTAs per SM with a 3-plane input
+    ring, 3 CTAs with a 2-plane ring) gather the level correctly."""
+    variant_guard.gamer_set_hydro_ctas_per_sm(mode, ctas)
+    _fused_vs_fill(mode, bc, dims)
+
+
+def _fused_vs_fill(mode, bc, dims):
     import torch
     from paper_1007_3818_gb300 import native
     gx, gy, gz = dims
