@@ -4,10 +4,11 @@
 Workload (default): a uniform periodic level of 16^3 patch groups = 4096
 groups, 256^3 cells, FP32, gamma = 5/3, rho = 1 + 0.1 * (8 seeded Fourier
 modes, |k| <= 8), p = 1, smooth Gaussian velocity of rms 0.3 c_s; every step
-fills the ghost zones from the neighbours on the device, advances all groups
-and reduces the next shared dt in FP64.  Synthetic data (seed 1007).
+advances all groups, each kernel CTA gathering its group's ghost zones from
+the neighbours' interiors, and reduces the next shared dt in FP64.  Synthetic
+data (seed 1007).
 
-One step = ghost fill + hydro step + dt reduction over the whole level.
+One step = hydro step (ghost gather fused in) + dt reduction over the level.
 value = cells updated per second over the timed steps (max time over ranks;
 each rank runs its own level: weak scaling).  e2e = the same groups through
 the host-buffer pipeline entry point, host<->device copies included.
@@ -42,6 +43,38 @@ GROUP_CELLS = 4096
 # (8 B each), status (4 B), partials (48 B)
 def group_bytes(esz):
     return (20480 + 20480 + 7680) * esz + 16 + 4 + 48
+
+
+# DRAM traffic of one launch of the FP32 fused level kernel on this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
+# `python -m paper_1007_3818_gb300.profile_case --path both --groups 16 16 16
+# --ctas 3`), valid for the kernel sources it was taken on only: reported as
+# null once any of them changes.
+KERNEL_SOURCES = ["paper_1007_3818_gb300/csrc/hydro_kernel.cuh",
+                  "paper_1007_3818_gb300/csrc/device_util.cuh",
+                  "paper_1007_3818_gb300/csrc/hydro_launch.cuh",
+                  "paper_1007_3818_gb300/csrc/hydro_f32.cu"]
+NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "ctas_per_sm": 3, "bytes": 782712576,
+               "sources_sha256": "ed49441c405d8df6d44d11376a081ee28246c02cec9cc0695ca89a7186af4fd1"}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(mode, groups, ctas_per_sm):
+    t = NCU_TRAFFIC
+    if (mode, groups, ctas_per_sm) != (t["mode"], t["groups"], t["ctas_per_sm"]):
+        return None
+    try:
+        return t["bytes"] if kernel_sources_sha256() == t["sources_sha256"] else None
+    except OSError:
+        return None
 
 
 SM_COUNT = 152
@@ -429,15 +462,17 @@ def main():
         v, cores, desc, flops_per_cell = cpu_baseline(tiles_host0, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     roofline = None
+    traffic = measured_traffic(args.mode, G, tuned_level["ctas_per_sm"])
     roofline_hbm = {
         "bound": "hbm", "achieved": G * group_bytes(esz) / adv_s / 1e9, "peak": hbm_peak,
         "unit": "GB/s", "frac": G * group_bytes(esz) / adv_s / 1e9 / hbm_peak,
-        "traffic": None, "note": "algorithmic bytes of the fused hydro kernel (level in, "
-                                 "state and face fluxes out) vs measured HBM copy"}
+        "traffic": traffic, "algorithmic_bytes": G * group_bytes(esz),
+        "note": "algorithmic bytes of the fused hydro kernel (level in, state and face "
+                "fluxes out) vs measured HBM copy"}
     if flops_per_cell is not None:
         ach = flops_per_cell * cells_per_step / adv_s / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                     "kernel": "hydro_step_kernel", "flops_per_cell": flops_per_cell,
                     "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"}
     if rank == 0:
