@@ -53,6 +53,7 @@ extern "C" {
 #define GAMER_ST_NONPOSITIVE_OUT    0x4u /* an updated cell has rho <= 0 or p <= 0 (or NaN)       */
 #define GAMER_ST_BAD_INPUT          0x8u /* non-finite read input, or dt < 0 / dh <= 0 / non-finite */
 #define GAMER_ST_INTERNAL_TIMEOUT  0x10u /* a bounded on-chip wait gave up; outputs are invalid  */
+#define GAMER_ST_FLOOR             0x20u /* a density or pressure floor changed an updated cell   */
 
 /* ---- precision modes ---- */
 #define GAMER_MODE_F32 0   /* FP32 storage and arithmetic                                     */
@@ -66,6 +67,11 @@ typedef struct gh_params {
     int32_t limiter;            /* slope limiter: 0 van Leer (default), 1 minmod, 2 MC      */
     int32_t predictor_fallback; /* 0: cell average (default), 1: un-evolved face states   */
     int32_t reserved[2];        /* must be 0                                                */
+    double rho_floor;           /* finite, >= 0; 0 = off (default): an updated density below
+                                   it is raised to it, momentum kept                         */
+    double p_floor;             /* finite, >= 0; 0 = off (default): where the updated density
+                                   is positive and the pressure below p_floor, the total
+                                   energy becomes |m|^2/(2 rho) + p_floor/(gamma - 1)        */
 } gh_params;
 
 /*

@@ -40,6 +40,7 @@ ST_PREDICTOR_FALLBACK = 1
 ST_HLLE_FALLBACK = 2
 ST_NONPOSITIVE_OUT = 4
 ST_BAD_INPUT = 8
+ST_FLOOR = 32
 
 
 def build(force: bool = False) -> str:
@@ -57,7 +58,8 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("limiter", ctypes.c_int32),
-                ("predictor_fallback", ctypes.c_int32)]
+                ("predictor_fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
+                ("p_floor", ctypes.c_double)]
 
 
 def _load():
@@ -101,15 +103,17 @@ def _ptr(a, ctype=ctypes.c_double):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def _params(gamma, limiter, predictor_fallback):
-    return _Params(float(gamma), int(limiter), int(predictor_fallback))
+def _params(gamma, limiter, predictor_fallback, rho_floor=0.0, p_floor=0.0):
+    return _Params(float(gamma), int(limiter), int(predictor_fallback), float(rho_floor),
+                   float(p_floor))
 
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0):
+def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_floor=0.0,
+                p_floor=0.0):
     """One step on a ghost-padded box U_in[5][nz+4][ny+4][nx+4].
 
     Returns (out[5][nz][ny][nx], face_flux (list of 6 arrays), status, partials[6])."""
@@ -120,7 +124,7 @@ def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0):
     ff = np.empty(2 * 5 * (nz * ny + nz * nx + ny * nx))
     st = np.zeros(1, dtype=np.uint32)
     part = np.empty(6)
-    p = _params(gamma, limiter, predictor_fallback)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor)
     rc = _load().oracle_advance_box(_ptr(U_in), nx, ny, nz, _ptr(out), _ptr(ff), float(dt),
                                     float(dh), ctypes.byref(p), _ptr(st, ctypes.c_uint32),
                                     _ptr(part))
@@ -135,7 +139,7 @@ def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0):
 
 
 def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nthreads=1,
-                   want_flux=True):
+                   want_flux=True, rho_floor=0.0, p_floor=0.0):
     """N independent patch groups U_in[N][5][20][20][20] (dt, dh scalars or [N]).
 
     Returns (out[N][5][16][16][16], face_flux[N][6][5][16][16] or None,
@@ -149,7 +153,7 @@ def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nth
     ff = np.empty((N, 6, 5, 16, 16)) if want_flux else None
     st = np.zeros(N, dtype=np.uint32)
     part = np.empty((N, 6))
-    p = _params(gamma, limiter, predictor_fallback)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor)
     rc = _load().oracle_advance_groups(_ptr(U_in), _ptr(out), _ptr(ff), _ptr(dt), _ptr(dh), N,
                                        ctypes.byref(p), _ptr(st, ctypes.c_uint32), _ptr(part),
                                        int(nthreads))

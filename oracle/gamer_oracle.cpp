@@ -29,6 +29,7 @@
 //      wave's side states being U_L and U*_L (wave 1), U*_R and U_R (wave 5);
 //   R7 HLLE fallback (Einfeldt speeds) when the Roe sound speed squared is not
 //      positive or either Roe intermediate state has rho <= 0 or p <= 0;
+//      without a Roe sound speed, Davis's bounds over both states;
 //   R9 no density or pressure floors;
 //   R11 face fluxes emitted as the raw physical flux used by the update.
 #include "gamer_oracle.h"
@@ -83,6 +84,8 @@ struct Scheme {
     R gm1;  // gamma - 1
     int limiter;
     int pred_fallback;
+    R rho_floor = R(0.0);  // 0: off
+    R p_floor = R(0.0);    // 0: off
 
     // Conserved -> primitive.  p = (gamma-1) (E - 0.5 |m|^2 / rho).
     void prim(const R U[5], R W[5]) const {
@@ -135,7 +138,9 @@ struct Scheme {
     }
 
     // READING R7: HLLE flux with Einfeldt speed estimates.  When the Roe state
-    // is usable (have_roe) its speeds widen the bounds.
+    // is usable (have_roe) its speeds widen the bounds u_L - c_L, u_R + c_R;
+    // without it, Davis's bounds over both states, which keep S_L < S_R also
+    // in a supersonic collision (u_L - c_L > 0 > u_R + c_R).
     void hlle(const R UL[5], const R UR[5], const R FL[5], const R FR[5], R uL, R cL, R uR,
               R cR, bool have_roe, R uT, R cT, R F[5]) const {
         R sl = uL - cL;
@@ -143,6 +148,9 @@ struct Scheme {
         if (have_roe) {
             sl = r_min(sl, uT - cT);
             sr = r_max(sr, uT + cT);
+        } else {
+            sl = r_min(sl, uR - cR);
+            sr = r_max(sr, uL + cL);
         }
         R bm = r_min(sl, R(0.0));
         R bp = r_max(sr, R(0.0));
@@ -386,8 +394,25 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
                     acc = acc + (FY(i, j + 1, k)[q] - FY(i, j, k)[q]);
                     acc = acc + (FZ(i, j, k + 1)[q] - FZ(i, j, k)[q]);
                     Un[q] = U[q] - lam * acc;
-                    out[q * ocells + ((std::size_t)k * ny + j) * nx + i] = Un[q];
                 }
+                // Optional floors on the updated state: density first (momentum
+                // kept), then pressure, by setting the total energy to the kinetic
+                // energy plus max(p_floor / (gamma - 1), 4 eps ke) where rho > 0 and
+                // p < p_floor (eps = 2^-52: the thermal part stays resolvable next
+                // to the kinetic energy, so the stored state keeps p > 0).
+                if (S.rho_floor > R(0.0) && Un[0] < S.rho_floor) {
+                    Un[0] = S.rho_floor;
+                    st |= ORACLE_ST_FLOOR;
+                }
+                if (S.p_floor > R(0.0) && Un[0] > R(0.0)) {
+                    const R ke = R(0.5) * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0];
+                    if (S.gm1 * (Un[4] - ke) < S.p_floor) {
+                        const R eth = S.p_floor / S.gm1, res = R(4.0 * 2.220446049250313e-16) * ke;
+                        Un[4] = ke + (eth > res ? eth : res);
+                        st |= ORACLE_ST_FLOOR;
+                    }
+                }
+                for (int q = 0; q < 5; ++q) out[q * ocells + ((std::size_t)k * ny + j) * nx + i] = Un[q];
                 // epilogue: positivity flag and the time-step / conservation partials
                 R Wn[5];
                 S.prim(Un, Wn);
@@ -436,12 +461,16 @@ Scheme<R> make_scheme(const oracle_params* p) {
     S.gm1 = R(p->gamma - 1.0);
     S.limiter = p->limiter;
     S.pred_fallback = p->predictor_fallback;
+    S.rho_floor = R(p->rho_floor);
+    S.p_floor = R(p->p_floor);
     return S;
 }
 
 bool params_ok(const oracle_params* p) {
     return p && std::isfinite(p->gamma) && p->gamma > 1.0 && p->limiter >= 0 && p->limiter <= 2 &&
-           (p->predictor_fallback == 0 || p->predictor_fallback == 1);
+           (p->predictor_fallback == 0 || p->predictor_fallback == 1) &&
+           std::isfinite(p->rho_floor) && p->rho_floor >= 0.0 && std::isfinite(p->p_floor) &&
+           p->p_floor >= 0.0;
 }
 
 // ---------------------------------------------------------------------------

@@ -34,6 +34,8 @@ typedef struct {
     double gamma;            /* ratio of specific heats, > 1                       */
     int32_t limiter;         /* 0 van Leer (harmonic), 1 minmod, 2 monotonised central */
     int32_t predictor_fallback; /* 0: cell average, 1: un-evolved reconstruction   */
+    double rho_floor;        /* >= 0; 0 = off: updated rho below it is raised to it  */
+    double p_floor;          /* >= 0; 0 = off: updated p below it is raised to it   */
 } oracle_params;
 
 /* status bits (per box / per group) */
@@ -41,6 +43,7 @@ typedef struct {
 #define ORACLE_ST_HLLE_FALLBACK      2u
 #define ORACLE_ST_NONPOSITIVE_OUT    4u
 #define ORACLE_ST_BAD_INPUT          8u
+#define ORACLE_ST_FLOOR             32u
 
 /* One step on a general ghost-padded box.  face_flux, status, partials may be
  * NULL.  partials[6] = { max over cells of max_d|v_d| + c, sum rho, sum mx,

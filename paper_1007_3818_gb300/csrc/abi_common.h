@@ -28,6 +28,9 @@ inline int check_params(const gh_params* p) {
     if (p->limiter < 0 || p->limiter > 2) return GAMER_E_PARAM;
     if (p->predictor_fallback != 0 && p->predictor_fallback != 1) return GAMER_E_PARAM;
     if (p->reserved[0] != 0 || p->reserved[1] != 0) return GAMER_E_PARAM;
+    if (!std::isfinite(p->rho_floor) || p->rho_floor < 0.0 || !std::isfinite(p->p_floor) ||
+        p->p_floor < 0.0)
+        return GAMER_E_PARAM;
     return GAMER_OK;
 }
 

@@ -64,6 +64,9 @@ struct KConst {
     T gamma, gm1;
     P gm1p;
     int limiter, pfb;
+    int floors;         // bit 0: density floor on, bit 1: pressure floor on
+    T rho_floor, p_floor;
+    P eth_floor;        // p_floor / (gamma - 1)
 };
 
 // row slot of a 16-wide face / flux array (see the bank note above)
@@ -83,6 +86,41 @@ __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KC
         return static_cast<T>(kc.gm1p * (static_cast<double>(E) - ke));
     } else {
         return kc.gm1 * (E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
+    }
+}
+
+// Optional floors on an updated state (kc.floors != 0): a density below
+// rho_floor is raised to it, momentum kept; then, where rho > 0 and
+// p < p_floor, the total energy becomes ke + max(p_floor / (gamma - 1),
+// 4 eps ke), ke = |m|^2 / (2 rho) and eps the storage type's machine epsilon:
+// the thermal part is never below what E can resolve next to ke, so the
+// stored state keeps p > 0 (MIXED evaluates ke in FP64).  ir = 1/rho and p
+// are updated to the final state.
+template <int MODE, class T, class P>
+__device__ __forceinline__ void apply_floors(T o[5], T& ir, T& p, const KConst<T, P>& kc,
+                                             uint32_t& st) {
+    if ((kc.floors & 1) && o[0] < kc.rho_floor) {
+        o[0] = kc.rho_floor;
+        ir = rcp_(o[0]);
+        p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+        st |= GAMER_ST_FLOOR;
+    }
+    if ((kc.floors & 2) && o[0] > T(0) && p < kc.p_floor) {
+        constexpr T kRes = T(4) * (sizeof(T) == 4 ? T(1.1920928955078125e-7)    // 2^-23
+                                                   : T(2.220446049250313e-16));  // 2^-52
+        if constexpr (MODE == GAMER_MODE_MIXED) {
+            const double rd = o[0];
+            double ird = ir;
+            ird = fma(ird, fma(-rd, ird, 1.0), ird);
+            const double a = o[1], b = o[2], c = o[3];
+            const double ke = 0.5 * (a * a + b * b + c * c) * ird;
+            o[4] = static_cast<T>(ke + fmax(kc.eth_floor, double(kRes) * ke));
+        } else {
+            const T ke = T(0.5) * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * ir;
+            o[4] = ke + max_(kc.eth_floor, kRes * ke);
+        }
+        p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+        st |= GAMER_ST_FLOOR;
     }
 }
 
@@ -167,8 +205,9 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
     const T q2 = uT * uT + vT * vT + wT * wT;
     const T cT2 = kc.gm1 * (HT - T(0.5) * q2);
     if (!(cT2 > T(0))) {
+        // no Roe sound speed: Davis's bounds over both states (S_L < S_R)
         st |= GAMER_ST_HLLE_FALLBACK;
-        hlle_rot(L, R, FL, FR, uL - cL, uR + cR, F);
+        hlle_rot(L, R, FL, FR, min_(uL - cL, uR - cR), max_(uR + cR, uL + cL), F);
         return;
     }
     const T cT = sqrt_(cT2);
@@ -287,7 +326,8 @@ __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KCons
 }
 
 // The HLLE fallback recomputed from the two states alone (rare path, one
-// out-of-line copy): Einfeldt speeds with the Roe speeds when c~^2 > 0.
+// out-of-line copy): Einfeldt speeds with the Roe speeds when c~^2 > 0,
+// Davis's bounds over both states otherwise.
 template <class T>
 struct RoeIO {
     T v[5];
@@ -318,6 +358,9 @@ __device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P
         const T cT = sqrt_(cT2);
         sl = min_(sl, uT - cT);
         sr = max_(sr, uT + cT);
+    } else {  // Davis's bounds over both states (S_L < S_R)
+        sl = min_(sl, uR - cR);
+        sr = max_(sr, uL + cL);
     }
     RoeIO<T> out;
     hlle_rot(L, R, FL, FR, sl, sr, out.v);
@@ -857,13 +900,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         const int jj = cc ? j1 : j0;
                         T o[5];
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) {
-                            o[q] = Ep[q] - lam * (fn[q] - fo[q]);
-                            gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
-                        }
-                        // epilogue: positivity flag, signal speed and sums
-                        const T ir = rcp_(o[0]);
-                        const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                        for (int q = 0; q < 5; ++q) o[q] = Ep[q] - lam * (fn[q] - fo[q]);
+                        // epilogue: floors, positivity flag, signal speed and sums
+                        T ir = rcp_(o[0]);
+                        T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                        if (kc.floors) apply_floors<MODE>(o, ir, p, kc, st);
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
                         if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
                         const T c2 = kc.gamma * p * ir;
                         const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);

@@ -53,6 +53,10 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     kc.gm1p = P(p->gamma - 1.0);
     kc.limiter = p->limiter;
     kc.pfb = p->predictor_fallback;
+    kc.floors = (p->rho_floor > 0.0 ? 1 : 0) | (p->p_floor > 0.0 ? 2 : 0);
+    kc.rho_floor = T(p->rho_floor);
+    kc.p_floor = T(p->p_floor);
+    kc.eth_floor = P(p->p_floor / (p->gamma - 1.0));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int want = hydro_ctas_per_sm_override(MODE);
     const int var = hydro_variant();

@@ -227,12 +227,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
                             const int kk = k - 2;
                             T o[5];
 #pragma unroll
-                            for (int q = 0; q < 5; ++q) {
-                                o[q] = Ec[q] - lam * (fn[q] - fo[q]);
+                            for (int q = 0; q < 5; ++q) o[q] = Ec[q] - lam * (fn[q] - fo[q]);
+                            T ir = rcp_(o[0]);
+                            T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                            if (kc.floors) apply_floors<MODE>(o, ir, p, kc, st);
+#pragma unroll
+                            for (int q = 0; q < 5; ++q)
                                 gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
-                            }
-                            const T ir = rcp_(o[0]);
-                            const T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
                             if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
                             const T c2 = kc.gamma * p * ir;
                             const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);

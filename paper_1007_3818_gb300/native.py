@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgamer_gb300.so")
 
 GAMER_MODE_F32, GAMER_MODE_MIXED, GAMER_MODE_F64 = 0, 1, 2
 ST_PREDICTOR_FALLBACK, ST_HLLE_FALLBACK, ST_NONPOSITIVE_OUT = 0x1, 0x2, 0x4
-ST_BAD_INPUT, ST_INTERNAL_TIMEOUT = 0x8, 0x10
+ST_BAD_INPUT, ST_INTERNAL_TIMEOUT, ST_FLOOR = 0x8, 0x10, 0x20
 
 _lock = threading.Lock()
 _lib = None
@@ -33,11 +33,13 @@ class GamerError(RuntimeError):
 class gh_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("limiter", ctypes.c_int32), ("predictor_fallback", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("reserved", ctypes.c_int32 * 2), ("rho_floor", ctypes.c_double),
+                ("p_floor", ctypes.c_double)]
 
 
-def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0):
-    return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback), (0, 0))
+def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0, rho_floor=0.0, p_floor=0.0):
+    return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback), (0, 0),
+                     float(rho_floor), float(p_floor))
 
 
 def lib():

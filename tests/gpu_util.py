@@ -23,7 +23,8 @@ def host_input(tiles, mode):
     return np.ascontiguousarray(tiles, dtype=np.float32).astype(np.float64)
 
 
-def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, with_flux=True):
+def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, with_flux=True,
+                rho_floor=0.0, p_floor=0.0):
     """One step on the GPU; returns numpy (out, face_flux, status, partials)."""
     import torch
     from paper_1007_3818_gb300 import native
@@ -36,7 +37,8 @@ def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, wit
     d_dh = torch.as_tensor(np.broadcast_to(np.asarray(dh, np.float64), (N,)).copy(), device="cuda")
     d_st = torch.full((N,), -1, device="cuda", dtype=torch.int32)
     d_part = torch.full((N, 6), float("nan"), device="cuda", dtype=torch.float64)
-    params = native.make_params(gamma, limiter=limiter, predictor_fallback=predictor_fallback)
+    params = native.make_params(gamma, limiter=limiter, predictor_fallback=predictor_fallback,
+                                rho_floor=rho_floor, p_floor=p_floor)
     native.hydro_advance(mode, d_in, d_out, d_ff, d_dt, d_dh, d_st, d_part, params)
     torch.cuda.synchronize()
     ff = d_ff.double().cpu().numpy() if with_flux else None

@@ -80,6 +80,9 @@ def test_advance_rejects_bad_arguments(lib, name):
     bad = native.make_params(1.4)
     bad.reserved[0] = 1
     assert _adv(lib, name, params=bad) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, rho_floor=-1e-3)) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, p_floor=float("nan"))) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, p_floor=float("inf"))) == -2
     assert _adv(lib, name, in_=FAKE + 8) == -3           # TMA source needs 16 B alignment
     assert _adv(lib, name, dt=FAKE + (2 << 30) + 4) == -3
     assert _adv(lib, name, out=FAKE + 64) == -6          # out inside in

@@ -328,6 +328,42 @@ def test_variant_uniform_state_bitwise(variant_guard, mode, variant):
 
 
 # --------------------------------------------------------------------------
+# Density and pressure floors on the updated state
+@pytest.mark.parametrize("mode", [F32, MIXED, F64], ids=["f32", "mixed", "f64"])
+def test_floors_match_oracle(mode):
+    g, rf, pf = 1.4, 1e-3, 1e-5
+    host = host_input(wl.stress_groups(3, seed=11, gamma=g), mode)
+    out, ff, st, part = gpu_advance(host, 0.02, 1 / 16, g, mode, rho_floor=rf, p_floor=pf)
+    r_out, r_ff, r_st, r_part = oracle.advance_groups(host, 0.02, 1 / 16, gamma=g, rho_floor=rf,
+                                                      p_floor=pf)
+    assert (r_st & oracle.ST_FLOOR).all()
+    assert ((st & native_st_floor()) != 0).all()
+    assert not (st & 4).any()
+    assert out[:, 0].min() >= np.float32(rf) * (1 - 1e-7)
+    if mode == F64:
+        assert np.array_equal(st, r_st)
+        assert rel_l1_fields(out, r_out) <= TOL_F64
+    else:
+        # a step this violent decides some floors within rounding of the threshold
+        assert rel_l1_fields(out, r_out) <= 1e-3
+
+
+@pytest.mark.parametrize("mode", [F32, F64], ids=["f32", "f64"])
+def test_floors_off_changes_nothing(mode):
+    g = 5 / 3
+    host = host_input(wl.random_smooth_groups(3, seed=21, gamma=g), mode)
+    a = gpu_advance(host, 2e-3, 1 / 256, g, mode)
+    b = gpu_advance(host, 2e-3, 1 / 256, g, mode, rho_floor=1e-20, p_floor=1e-20)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def native_st_floor():
+    from paper_1007_3818_gb300 import native
+    return native.ST_FLOOR
+
+
+# --------------------------------------------------------------------------
 # Fused ghost gather: the level read directly by the step kernel
 @pytest.mark.parametrize("mode", [F32, MIXED, F64], ids=["f32", "mixed", "f64"])
 @pytest.mark.parametrize("bc", [0, 1])

@@ -506,6 +506,50 @@ def test_fallbacks_keep_strong_rarefactions_positive():
     assert W[:, 0].min() > 0 and W[:, 4].min() > 0
 
 
+def test_floors_are_inert_when_not_reached():
+    """Floors act only on cells below them: far-away floors leave every output
+    bit unchanged, and none is flagged."""
+    g = 5 / 3
+    t = wl.random_smooth_groups(2, seed=3, gamma=g)
+    a = oracle.advance_groups(t, 2e-3, 1 / 64, gamma=g)
+    b = oracle.advance_groups(t, 2e-3, 1 / 64, gamma=g, rho_floor=1e-12, p_floor=1e-12)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert not (b[2] & oracle.ST_FLOOR).any()
+
+
+def _pressure(o, g):
+    return (g - 1) * (o[:, 4] - 0.5 * (o[:, 1] ** 2 + o[:, 2] ** 2 + o[:, 3] ** 2) / o[:, 0])
+
+
+def test_floors_raise_density_then_pressure_after_the_update():
+    """A step that drives cells to negative density and pressure: with floors,
+    (i) fluxes and momenta are those of the unfloored step (the floors act on
+    the updated state only); (ii) density is max(rho, rho_floor) cell by
+    cell; (iii) the energy changes exactly where the pressure of the
+    density-floored state is below p_floor, and there the pressure becomes
+    p_floor (up to the rounding of E - |m|^2/(2 rho)); (iv) no cell is left
+    non-positive and the floor bit is set."""
+    g, rf, pf = 1.4, 1e-3, 1e-5
+    t = wl.stress_groups(3, seed=11, gamma=g)
+    o0, f0, s0, _ = oracle.advance_groups(t, 0.02, 1 / 16, gamma=g)
+    o1, f1, s1, p1 = oracle.advance_groups(t, 0.02, 1 / 16, gamma=g, rho_floor=rf, p_floor=pf)
+    assert (s0 & oracle.ST_NONPOSITIVE_OUT).all()
+    assert (s1 & oracle.ST_FLOOR).all() and not (s1 & oracle.ST_NONPOSITIVE_OUT).any()
+    assert np.array_equal(f0, f1) and np.array_equal(o0[:, 1:4], o1[:, 1:4])
+    assert np.array_equal(o1[:, 0], np.where(o0[:, 0] < rf, rf, o0[:, 0]))
+    mid = o0.copy()
+    mid[:, 0] = o1[:, 0]
+    raised = _pressure(mid, g) < pf
+    assert raised.any() and np.array_equal(o1[:, 4] != o0[:, 4], raised)
+    p_after = _pressure(o1, g)
+    assert np.all(np.abs(p_after[raised] - pf) <= 4 * (g - 1) * np.spacing(o1[:, 4][raised]) +
+                  1e-12 * pf)
+    assert np.all(p_after[~raised] >= pf)
+    # the partials see the floored state
+    assert np.allclose(p1[:, 1], o1[:, 0].reshape(3, -1).sum(1), rtol=1e-13)
+
+
 def test_hydro_dt_and_totals_hand_example():
     part = np.array([[2.0, 1, 2, 3, 4, 5], [4.0, 1, 1, 1, 1, 1], [1.0, 0, 0, 0, 0, 1]])
     dt, tot = oracle.hydro_dt(part, [0.1, 0.05], 0.5, level=[0, 0, 1])
