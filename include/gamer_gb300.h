@@ -66,7 +66,12 @@ typedef struct gh_params {
     double cfl;                 /* Courant number; used only by gamer_hydro_dt's callers    */
     int32_t limiter;            /* slope limiter: 0 van Leer (default), 1 minmod, 2 MC      */
     int32_t predictor_fallback; /* 0: cell average (default), 1: un-evolved face states   */
-    int32_t reserved[2];        /* must be 0                                                */
+    int32_t flux_layout;        /* face_flux per group: 0 = the six group faces [6][5][16][16]
+                                   (default); 1 = nine planes [9][5][16][16], three per
+                                   direction at 0, 8 and 16 cells (x: 0,1,2; y: 3,4,5;
+                                   z: 6,7,8), which adds the patch boundaries inside the
+                                   group for the coarse-fine flux fix-up                   */
+    int32_t reserved;           /* must be 0                                                */
     double rho_floor;           /* finite, >= 0; 0 = off (default): an updated density below
                                    it is raised to it, momentum kept                         */
     double p_floor;             /* finite, >= 0; 0 = off (default): where the updated density
@@ -89,8 +94,11 @@ typedef struct gh_params {
  *   face_flux [N][6][5][16][16] raw numerical flux F (not multiplied by dt)
  *             through the six group faces, in the order -x, +x, -y, +y, -z, +z;
  *             the two in-face indices are [k][j] for x faces, [k][i] for y
- *             faces, [j][i] for z faces.  For the AMR coarse-fine flux fix-up.
- *             May be NULL.
+ *             faces, [j][i] for z faces.  With p->flux_layout = 1,
+ *             [N][9][5][16][16]: per direction the planes at 0, 8 and 16
+ *             cells (the group faces and the patch boundary between them), in
+ *             the order x0, x8, x16, y0, y8, y16, z0, z8, z16.  For the AMR
+ *             coarse-fine flux fix-up (gamer_flux_fixup_*).  May be NULL.
  *   dt, dh    [N] time step and cell width of each group (FP64).
  *   status    [N] GAMER_ST_* bits, or NULL.
  *   partials  [N][6] FP64: { max over updated cells of max_d |v_d| + c,
@@ -307,6 +315,75 @@ int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
  * shared memory, branch-free Roe path, compile-time limiter; 2 CTAs per SM in
  * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide setting. */
 int gamer_set_hydro_variant(int32_t variant);
+
+/*
+ * AMR coarse-fine coupling after one coarse step and its fine sub-steps: the
+ * step that consumes the face fluxes of gamer_hydro_advance_*.  The paper
+ * relies on GAMER's AMR structure (Sec. 1) without describing this coupling;
+ * it is the conservative refluxing of Berger & Colella (1989) for refinement
+ * ratio 2, where one fine patch group (16^3 fine cells) covers one octant
+ * (8^3 cells) of a coarse patch group, so every coarse-fine interface lies on
+ * a coarse group's flux plane at 0, 8 or 16 cells (flux_layout 1).
+ *
+ * gamer_cf_face: the 8x8 coarse faces of quadrant `quadrant` (bit 0: in-plane
+ * index a from 8, bit 1: b from 8; [a][b] = [k][j] for x planes, [k][i] for y,
+ * [j][i] for z) of plane `plane` (0, 1, 2 = 0, 8, 16 cells) along `dir` (0 x,
+ * 1 y, 2 z) of coarse group `coarse`, covered by one face of fine group
+ * `fine`.  side 1: the fine region lies on the + side of the corrected coarse
+ * cells (layer 8*plane - 1; the fine group's -dir face); side 0: on their -
+ * side (layer 8*plane; its +dir face).  Valid: plane >= 1 for side 1,
+ * plane <= 1 for side 0.
+ * gamer_cf_child: fine group `fine` covers octant `octant` (bit 0: x from 8,
+ * bit 1: y, bit 2: z) of coarse group `coarse`; reserved = 0.
+ */
+typedef struct gamer_cf_face {
+    int64_t coarse, fine;
+    int32_t dir, plane, side, quadrant;
+} gamer_cf_face;
+typedef struct gamer_cf_child {
+    int64_t coarse, fine;
+    int32_t octant, reserved;
+} gamer_cf_child;
+
+/*
+ * gamer_flux_fixup_{f32,f64}: each coarse cell beside a fine region gets
+ *   U += s * (dt/dh)[coarse] * (F_c - <F_f>),  s = +1 (side 1) or -1 (side 0),
+ * F_c its face flux from the coarse step and <F_f> the mean of the 2x2 fine
+ * face fluxes over the n_sub equal fine sub-steps.  In place on the coarse
+ * groups' updated state; applied class by class (2*dir + side = 0..5), so a
+ * cell beside fine regions on several sides is corrected in that fixed order.
+ * Arithmetic in FP64, rounded once per class to the storage type (mixed mode
+ * uses _f32).
+ *   coarse       [Nc][5][16][16][16] updated coarse state (in/out).
+ *   coarse_flux  [Nc][9][5][16][16] the coarse step's face fluxes, flux_layout 1.
+ *   fine_flux    [n_sub][Nf][6][5][16][16] the fine sub-steps' face fluxes.
+ *   dt, dh       [Nc] the coarse groups' step and cell width (FP64).
+ *   faces        [n_faces] records (device memory, 8-byte aligned).
+ *   bad          device int32 or NULL: incremented once per invalid record
+ *                (out-of-range index or field); such records are skipped.
+ * All arrays are device memory; coarse must not overlap any input.  Returns
+ * GAMER_OK, GAMER_E_PARAM (negative sizes, n_sub < 1), GAMER_E_NULL,
+ * GAMER_E_ALIGN, GAMER_E_OVERLAP, GAMER_E_CUDA.  Asynchronous on `stream`.
+ *
+ * gamer_restrict_{f32,f64}: every coarse cell of a covered octant becomes the
+ * mean of its 2x2x2 fine cells (FP64 sum in z, y, x order, times 1/8, rounded
+ * once).  fine [Nf][5][16]^3, coarse [Nc][5][16]^3 (output; must not overlap
+ * fine or the records), children [n_children] (device memory), bad as above.
+ */
+int gamer_flux_fixup_f32(float* coarse, const float* coarse_flux, const float* fine_flux,
+                         int32_t n_sub, const double* dt, const double* dh, int64_t Nc,
+                         int64_t Nf, const gamer_cf_face* faces, int64_t n_faces, int32_t* bad,
+                         void* stream);
+int gamer_flux_fixup_f64(double* coarse, const double* coarse_flux, const double* fine_flux,
+                         int32_t n_sub, const double* dt, const double* dh, int64_t Nc,
+                         int64_t Nf, const gamer_cf_face* faces, int64_t n_faces, int32_t* bad,
+                         void* stream);
+int gamer_restrict_f32(const float* fine, float* coarse, int64_t Nc, int64_t Nf,
+                       const gamer_cf_child* children, int64_t n_children, int32_t* bad,
+                       void* stream);
+int gamer_restrict_f64(const double* fine, double* coarse, int64_t Nc, int64_t Nf,
+                       const gamer_cf_child* children, int64_t n_children, int32_t* bad,
+                       void* stream);
 
 /* Throughput probes for the roofline denominators (not part of the scheme).
  * kind 0: FP32 FMA, 1: FP64 FMA, 2: FP32 MUFU reciprocal -- a grid of

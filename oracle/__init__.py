@@ -59,7 +59,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("limiter", ctypes.c_int32),
                 ("predictor_fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
-                ("p_floor", ctypes.c_double)]
+                ("p_floor", ctypes.c_double), ("flux_layout", ctypes.c_int32)]
 
 
 def _load():
@@ -89,6 +89,11 @@ def _load():
         lib.oracle_exact_riemann_star.argtypes = [d, d, d, d, d, d, d, pd]
         lib.oracle_exact_riemann_sample.argtypes = [d, d, d, d, d, d, d, d, pd]
         lib.oracle_count_ops_group.argtypes = [pd, d, d, P(_Params), pd]
+        vp = ctypes.c_void_p
+        lib.oracle_flux_fixup.argtypes = [pd, pd, pd, ctypes.c_int, pd, pd, i64, i64, vp, i64]
+        lib.oracle_flux_fixup.restype = i64
+        lib.oracle_restrict.argtypes = [pd, pd, i64, i64, vp, i64]
+        lib.oracle_restrict.restype = i64
         for name in ("oracle_advance_box", "oracle_advance_groups", "oracle_fill_ghosts_uniform",
                      "oracle_hydro_dt", "oracle_roe_flux", "oracle_exact_riemann_star",
                      "oracle_count_ops_group"):
@@ -103,9 +108,9 @@ def _ptr(a, ctype=ctypes.c_double):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def _params(gamma, limiter, predictor_fallback, rho_floor=0.0, p_floor=0.0):
+def _params(gamma, limiter, predictor_fallback, rho_floor=0.0, p_floor=0.0, flux_layout=0):
     return _Params(float(gamma), int(limiter), int(predictor_fallback), float(rho_floor),
-                   float(p_floor))
+                   float(p_floor), int(flux_layout))
 
 
 def _f64(a):
@@ -113,25 +118,28 @@ def _f64(a):
 
 
 def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_floor=0.0,
-                p_floor=0.0):
+                p_floor=0.0, flux_layout=0):
     """One step on a ghost-padded box U_in[5][nz+4][ny+4][nx+4].
 
-    Returns (out[5][nz][ny][nx], face_flux (list of 6 arrays), status, partials[6])."""
+    Returns (out[5][nz][ny][nx], face_flux (list of 6 arrays: -x, +x, -y, +y,
+    -z, +z; or of 9 with flux_layout=1: x at 0, nx/2, nx, then y, then z),
+    status, partials[6])."""
     U_in = _f64(U_in)
     _, pz, py, px = U_in.shape
     nx, ny, nz = px - 4, py - 4, pz - 4
     out = np.empty((5, nz, ny, nx))
-    ff = np.empty(2 * 5 * (nz * ny + nz * nx + ny * nx))
+    per = 3 if flux_layout == 1 else 2
+    ff = np.empty(per * 5 * (nz * ny + nz * nx + ny * nx))
     st = np.zeros(1, dtype=np.uint32)
     part = np.empty(6)
-    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout)
     rc = _load().oracle_advance_box(_ptr(U_in), nx, ny, nz, _ptr(out), _ptr(ff), float(dt),
                                     float(dh), ctypes.byref(p), _ptr(st, ctypes.c_uint32),
                                     _ptr(part))
     if rc != 0:
         raise ValueError(f"oracle_advance_box rejected its arguments (rc={rc})")
     faces, o = [], 0
-    for shape in ((5, nz, ny),) * 2 + ((5, nz, nx),) * 2 + ((5, ny, nx),) * 2:
+    for shape in ((5, nz, ny),) * per + ((5, nz, nx),) * per + ((5, ny, nx),) * per:
         n = int(np.prod(shape))
         faces.append(ff[o:o + n].reshape(shape))
         o += n
@@ -139,10 +147,10 @@ def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_fl
 
 
 def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nthreads=1,
-                   want_flux=True, rho_floor=0.0, p_floor=0.0):
+                   want_flux=True, rho_floor=0.0, p_floor=0.0, flux_layout=0):
     """N independent patch groups U_in[N][5][20][20][20] (dt, dh scalars or [N]).
 
-    Returns (out[N][5][16][16][16], face_flux[N][6][5][16][16] or None,
+    Returns (out[N][5][16][16][16], face_flux[N][6 or 9][5][16][16] or None,
     status[N] uint32, partials[N][6])."""
     U_in = _f64(U_in)
     N = U_in.shape[0]
@@ -150,16 +158,59 @@ def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nth
     dt = _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (N,)))
     dh = _f64(np.broadcast_to(np.asarray(dh, dtype=np.float64), (N,)))
     out = np.empty((N, 5, 16, 16, 16))
-    ff = np.empty((N, 6, 5, 16, 16)) if want_flux else None
+    ff = np.empty((N, 9 if flux_layout == 1 else 6, 5, 16, 16)) if want_flux else None
     st = np.zeros(N, dtype=np.uint32)
     part = np.empty((N, 6))
-    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout)
     rc = _load().oracle_advance_groups(_ptr(U_in), _ptr(out), _ptr(ff), _ptr(dt), _ptr(dh), N,
                                        ctypes.byref(p), _ptr(st, ctypes.c_uint32), _ptr(part),
                                        int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_advance_groups rejected its arguments (rc={rc})")
     return out, ff, st, part
+
+
+def _records(a, names, itemsize):
+    a = np.ascontiguousarray(a)
+    assert a.dtype.names == names and a.dtype.itemsize == itemsize, a.dtype
+    return a
+
+
+def flux_fixup(coarse, coarse_flux, fine_flux, dt, dh, faces):
+    """Coarse-fine flux fix-up on a copy of coarse[Nc][5][16][16][16].
+
+    coarse_flux[Nc][9][5][16][16] (nine-plane layout), fine_flux
+    [n_sub][Nf][6][5][16][16] (the fine groups' sub-steps), dt, dh [Nc] (or
+    scalars), faces: records (coarse, fine, dir, plane, side, quadrant).
+    Returns (corrected coarse, number of invalid records)."""
+    out = _f64(coarse).copy()
+    Nc = out.shape[0]
+    cf = _f64(coarse_flux)
+    ff = _f64(fine_flux)
+    n_sub, Nf = ff.shape[0], ff.shape[1]
+    assert cf.shape == (Nc, 9, 5, 16, 16) and ff.shape[2:] == (6, 5, 16, 16)
+    dt = _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (Nc,)))
+    dh = _f64(np.broadcast_to(np.asarray(dh, dtype=np.float64), (Nc,)))
+    faces = _records(faces, ("coarse", "fine", "dir", "plane", "side", "quadrant"), 32)
+    bad = _load().oracle_flux_fixup(_ptr(out), _ptr(cf), _ptr(ff), int(n_sub), _ptr(dt),
+                                    _ptr(dh), Nc, Nf, faces.ctypes.data_as(ctypes.c_void_p),
+                                    len(faces))
+    if bad < 0:
+        raise ValueError("oracle_flux_fixup rejected its arguments")
+    return out, int(bad)
+
+
+def restrict(fine, coarse, children):
+    """Restriction of fine[Nf][5][16]^3 into a copy of coarse[Nc][5][16]^3 by
+    the child records (coarse, fine, octant, reserved).  Returns (coarse, bad)."""
+    out = _f64(coarse).copy()
+    fine = _f64(fine)
+    children = _records(children, ("coarse", "fine", "octant", "reserved"), 24)
+    bad = _load().oracle_restrict(_ptr(fine), _ptr(out), out.shape[0], fine.shape[0],
+                                  children.ctypes.data_as(ctypes.c_void_p), len(children))
+    if bad < 0:
+        raise ValueError("oracle_restrict rejected its arguments")
+    return out, int(bad)
 
 
 def fill_ghosts_uniform(level, gx, gy, gz, bc):

@@ -86,6 +86,7 @@ struct Scheme {
     int pred_fallback;
     R rho_floor = R(0.0);  // 0: off
     R p_floor = R(0.0);    // 0: off
+    int flux_layout = 0;   // 0: six box faces, 1: nine planes
 
     // Conserved -> primitive.  p = (gamma-1) (E - 0.5 |m|^2 / rho).
     void prim(const R U[5], R W[5]) const {
@@ -424,8 +425,23 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
                 for (int q = 0; q < 5; ++q) sums[q] = sums[q] + Un[q];
             }
 
-    // Coarse-fine face fluxes: raw flux on the six box faces.
-    if (ff) {
+    // Coarse-fine face fluxes: raw flux on the six box faces, or on nine planes
+    // (per direction at 0, n/2 and n cells: the faces and the patch boundary).
+    if (ff && S.flux_layout == 1) {
+        R* p = ff;
+        for (int f : {0, nx / 2, nx})  // x planes : [v][k][j]
+            for (int q = 0; q < 5; ++q)
+                for (int k = 0; k < nz; ++k)
+                    for (int j = 0; j < ny; ++j) *p++ = FX(f, j, k)[q];
+        for (int f : {0, ny / 2, ny})  // y planes : [v][k][i]
+            for (int q = 0; q < 5; ++q)
+                for (int k = 0; k < nz; ++k)
+                    for (int i = 0; i < nx; ++i) *p++ = FY(i, f, k)[q];
+        for (int f : {0, nz / 2, nz})  // z planes : [v][j][i]
+            for (int q = 0; q < 5; ++q)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) *p++ = FZ(i, j, f)[q];
+    } else if (ff) {
         R* p = ff;
         for (int side = 0; side < 2; ++side) {  // -x, +x : [v][k][j]
             const int f = side ? nx : 0;
@@ -463,6 +479,7 @@ Scheme<R> make_scheme(const oracle_params* p) {
     S.pred_fallback = p->predictor_fallback;
     S.rho_floor = R(p->rho_floor);
     S.p_floor = R(p->p_floor);
+    S.flux_layout = p->flux_layout;
     return S;
 }
 
@@ -470,7 +487,7 @@ bool params_ok(const oracle_params* p) {
     return p && std::isfinite(p->gamma) && p->gamma > 1.0 && p->limiter >= 0 && p->limiter <= 2 &&
            (p->predictor_fallback == 0 || p->predictor_fallback == 1) &&
            std::isfinite(p->rho_floor) && p->rho_floor >= 0.0 && std::isfinite(p->p_floor) &&
-           p->p_floor >= 0.0;
+           p->p_floor >= 0.0 && (p->flux_layout == 0 || p->flux_layout == 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -503,6 +520,7 @@ int oracle_advance_box(const double* in, int nx, int ny, int nz, double* out, do
                        double dt, double dh, const oracle_params* p, uint32_t* status,
                        double* partials) {
     if (!in || !out || !params_ok(p) || nx < 1 || ny < 1 || nz < 1) return -1;
+    if (p->flux_layout == 1 && ((nx | ny | nz) & 1)) return -1;
     Scheme<double> S = make_scheme<double>(p);
     return advance_box<double>(S, in, nx, ny, nz, out, face_flux, dt, dh, status, partials);
 }
@@ -518,7 +536,8 @@ int oracle_advance_groups(const double* in, double* out, double* face_flux, cons
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
     for (int64_t g = 0; g < N; ++g) {
         advance_box<double>(S, in + g * 40000, 16, 16, 16, out + g * 20480,
-                            face_flux ? face_flux + g * 7680 : nullptr, dt[g], dh[g],
+                            face_flux ? face_flux + g * (p->flux_layout ? 11520 : 7680) : nullptr,
+                            dt[g], dh[g],
                             status ? status + g : nullptr, partials ? partials + g * 6 : nullptr);
     }
     return 0;
@@ -706,6 +725,97 @@ int oracle_count_ops_group(const double* in, double dt, double dh, const oracle_
     counts[4] = g_tally.cmp;
     counts[5] = 4096.0;
     return 0;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// AMR coarse-fine coupling (the step after the hydro path): flux fix-up and
+// restriction, written as plain loops over the records.
+extern "C" {
+
+int64_t oracle_flux_fixup(double* coarse, const double* coarse_flux, const double* fine_flux,
+                          int n_sub, const double* dt, const double* dh, int64_t Nc, int64_t Nf,
+                          const oracle_cf_face* faces, int64_t n) {
+    if (n < 0 || Nc < 0 || Nf < 0 || n_sub < 1) return -1;
+    if (n == 0) return 0;
+    if (!coarse || !coarse_flux || !fine_flux || !dt || !dh || !faces) return -1;
+    int64_t bad = 0;
+    for (int cls = 0; cls < 6; ++cls) {
+        for (int64_t r = 0; r < n; ++r) {
+            const oracle_cf_face& F = faces[r];
+            const bool ok = F.coarse >= 0 && F.coarse < Nc && F.fine >= 0 && F.fine < Nf &&
+                            F.dir >= 0 && F.dir <= 2 && F.plane >= 0 && F.plane <= 2 &&
+                            (F.side == 0 || F.side == 1) && F.quadrant >= 0 && F.quadrant <= 3 &&
+                            !(F.side == 1 && F.plane == 0) && !(F.side == 0 && F.plane == 2);
+            if (!ok) {
+                if (cls == 0) ++bad;
+                continue;
+            }
+            if (2 * F.dir + F.side != cls) continue;
+            const double lam = dt[F.coarse] / dh[F.coarse];
+            const int layer = F.side ? 8 * F.plane - 1 : 8 * F.plane;
+            const int fface = 2 * F.dir + (F.side ? 0 : 1);  // the fine group's face
+            const int a0 = (F.quadrant & 1) ? 8 : 0, b0 = (F.quadrant & 2) ? 8 : 0;
+            const double* Fc = coarse_flux + ((std::size_t)F.coarse * 9 + 3 * F.dir + F.plane) * 1280;
+            double* U = coarse + (std::size_t)F.coarse * 20480;
+            for (int q = 0; q < 5; ++q)
+                for (int a = a0; a < a0 + 8; ++a)
+                    for (int b = b0; b < b0 + 8; ++b) {
+                        double sum = 0.0;
+                        for (int s = 0; s < n_sub; ++s) {
+                            const double* Ff =
+                                fine_flux + (((std::size_t)s * Nf + F.fine) * 6 + fface) * 1280 +
+                                (std::size_t)q * 256;
+                            for (int A = 2 * (a - a0); A < 2 * (a - a0) + 2; ++A)
+                                for (int B = 2 * (b - b0); B < 2 * (b - b0) + 2; ++B)
+                                    sum = sum + Ff[A * 16 + B];
+                        }
+                        const double mean = sum / double(4 * n_sub);
+                        const double corr = lam * (Fc[q * 256 + a * 16 + b] - mean);
+                        int i, j, k;
+                        if (F.dir == 0) { k = a; j = b; i = layer; }
+                        else if (F.dir == 1) { k = a; i = b; j = layer; }
+                        else { j = a; i = b; k = layer; }
+                        double& u = U[((q * 16 + k) * 16 + j) * 16 + i];
+                        u = F.side ? u + corr : u - corr;
+                    }
+        }
+    }
+    return bad;
+}
+
+int64_t oracle_restrict(const double* fine, double* coarse, int64_t Nc, int64_t Nf,
+                        const oracle_cf_child* children, int64_t n) {
+    if (n < 0 || Nc < 0 || Nf < 0) return -1;
+    if (n == 0) return 0;
+    if (!fine || !coarse || !children) return -1;
+    int64_t bad = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        const oracle_cf_child& C = children[r];
+        if (!(C.coarse >= 0 && C.coarse < Nc && C.fine >= 0 && C.fine < Nf && C.octant >= 0 &&
+              C.octant <= 7)) {
+            ++bad;
+            continue;
+        }
+        const int ox = (C.octant & 1) ? 8 : 0, oy = (C.octant & 2) ? 8 : 0,
+                  oz = (C.octant & 4) ? 8 : 0;
+        const double* f = fine + (std::size_t)C.fine * 20480;
+        double* c = coarse + (std::size_t)C.coarse * 20480;
+        for (int q = 0; q < 5; ++q)
+            for (int k = 0; k < 8; ++k)
+                for (int j = 0; j < 8; ++j)
+                    for (int i = 0; i < 8; ++i) {
+                        double sum = 0.0;
+                        for (int dk = 0; dk < 2; ++dk)
+                            for (int dj = 0; dj < 2; ++dj)
+                                for (int di = 0; di < 2; ++di)
+                                    sum = sum + f[((q * 16 + 2 * k + dk) * 16 + 2 * j + dj) * 16 +
+                                                  2 * i + di];
+                        c[((q * 16 + oz + k) * 16 + oy + j) * 16 + ox + i] = sum * 0.125;
+                    }
+    }
+    return bad;
 }
 
 }  // extern "C"

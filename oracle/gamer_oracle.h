@@ -36,6 +36,8 @@ typedef struct {
     int32_t predictor_fallback; /* 0: cell average, 1: un-evolved reconstruction   */
     double rho_floor;        /* >= 0; 0 = off: updated rho below it is raised to it  */
     double p_floor;          /* >= 0; 0 = off: updated p below it is raised to it   */
+    int32_t flux_layout;     /* 0: six box faces; 1: nine planes, three per direction
+                                at 0, n/2 and n cells (n even)                       */
 } oracle_params;
 
 /* status bits (per box / per group) */
@@ -54,7 +56,7 @@ int oracle_advance_box(const double* in, int nx, int ny, int nz, double* out,
                        uint32_t* status, double* partials);
 
 /* N independent 16^3 patch groups: in[N][5][20][20][20], out[N][5][16][16][16],
- * face_flux[N][6][5][16][16] (or NULL), dt[N], dh[N], status[N] (or NULL),
+ * face_flux[N][6 or 9][5][16][16] (or NULL), dt[N], dh[N], status[N] (or NULL),
  * partials[N][6] (or NULL).  nthreads > 1 spreads groups over OpenMP threads. */
 int oracle_advance_groups(const double* in, double* out, double* face_flux,
                           const double* dt, const double* dh, int64_t N,
@@ -74,6 +76,46 @@ int oracle_fill_ghosts_uniform(const double* level, int gx, int gy, int gz, int 
 int oracle_hydro_dt(const double* partials, int64_t N, const int32_t* level,
                     int32_t n_levels, const double* dh_level, double cfl,
                     double* dt_out, double* totals);
+
+/* ---- AMR coarse-fine coupling after a coarse step and its fine sub-steps ----
+ * Geometry: refinement ratio 2; a fine patch group (16^3 fine cells) covers one
+ * octant (8^3 cells) of a coarse patch group, so coarse-fine interfaces lie on
+ * the coarse groups' flux planes at 0, 8 or 16 cells (flux_layout 1).
+ *
+ * One interface record: the 8x8 coarse faces of quadrant `quadrant` (bit 0: in-
+ * plane index a from 8, bit 1: b from 8; [a][b] = [k][j] for x planes, [k][i]
+ * for y, [j][i] for z) of plane `plane` (0, 1, 2) along `dir` of coarse group
+ * `coarse`, covered by one face of fine group `fine`.  side 1: the fine region
+ * lies on the + side of the corrected coarse cells (layer 8*plane - 1; the fine
+ * group's -dir face); side 0: on their - side (layer 8*plane; its +dir face). */
+typedef struct {
+    int64_t coarse, fine;
+    int32_t dir, plane, side, quadrant;
+} oracle_cf_face;
+
+/* Flux fix-up (refluxing, Berger & Colella 1989): each coarse cell beside a
+ * fine region gets U += s * (dt/dh)_coarse * (F_c - <F_f>), s = +1 for side 1
+ * and -1 for side 0, F_c its coarse face flux (coarse_flux [Nc][9][5][16][16])
+ * and <F_f> the mean of the 2x2 fine face fluxes over the n_sub equal sub-steps
+ * (fine_flux [n_sub][Nf][6][5][16][16]).  Records are applied class by class
+ * (2*dir + side = 0..5), each class in record order.  Returns the number of
+ * invalid records (skipped) or -1 on a bad argument. */
+int64_t oracle_flux_fixup(double* coarse, const double* coarse_flux, const double* fine_flux,
+                          int n_sub, const double* dt, const double* dh, int64_t Nc, int64_t Nf,
+                          const oracle_cf_face* faces, int64_t n);
+
+/* One child record: fine group `fine` covers octant `octant` (bit 0: x from 8,
+ * bit 1: y, bit 2: z) of coarse group `coarse`. */
+typedef struct {
+    int64_t coarse, fine;
+    int32_t octant, reserved;
+} oracle_cf_child;
+
+/* Restriction: each coarse cell of a covered octant becomes the mean of its
+ * 2x2x2 fine cells (conservative average).  fine [Nf][5][16]^3, coarse
+ * [Nc][5][16]^3.  Returns the number of invalid records or -1. */
+int64_t oracle_restrict(const double* fine, double* coarse, int64_t Nc, int64_t Nf,
+                        const oracle_cf_child* children, int64_t n);
 
 /* ---- pieces, exposed for unit pins ---- */
 void oracle_prim_from_cons(const double U[5], double gamma, double W[5]);

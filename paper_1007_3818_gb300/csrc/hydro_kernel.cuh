@@ -64,6 +64,7 @@ struct KConst {
     T gamma, gm1;
     P gm1p;
     int limiter, pfb;
+    int flux9;          // face-flux layout: 0 six group faces, 1 nine planes
     int floors;         // bit 0: density floor on, bit 1: pressure floor on
     T rho_floor, p_floor;
     P eth_floor;        // p_floor / (gamma - 1)
@@ -71,6 +72,16 @@ struct KConst {
 
 // row slot of a 16-wide face / flux array (see the bank note above)
 __device__ __forceinline__ int frow(int j) { return j ^ ((j >> 2) & 1); }
+
+// Face-flux plane of the face at cell index b in [0, 16] along direction dir
+// (the face between cells b-1 and b), or -1 when the layout does not store it:
+// six group faces (-x, +x, -y, +y, -z, +z) or nine planes (b = 0, 8, 16 per
+// direction).
+__device__ __forceinline__ int flux_plane(int dir, int b, int flux9) {
+    if (flux9) return (b & 7) ? -1 : 3 * dir + (b >> 3);
+    return (b == 0) ? 2 * dir : (b == 16) ? 2 * dir + 1 : -1;
+}
+constexpr int kFluxPlane = 5 * 256;  // one plane: [5][16][16]
 
 // ---------------------------------------------------------------------------
 // Pressure from a conserved state, given 1/rho in T.  MIXED recovers it in
@@ -821,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         const PlaneLoader<SRC, RING, T> loader(in, g, geo, gplan);
         auto load_plane = [&](int kp) { loader.load(S, kp); };
         T* gout = out + g * 20480;
-        T* gff = face_flux ? face_flux + g * 7680 : nullptr;
+        T* gff = face_flux ? face_flux + g * (kc.flux9 ? 9 : 6) * kFluxPlane : nullptr;
         const double dtg = dt[g], dhg = dh[g];
         const T lam = static_cast<T>(dtg / dhg);
         const T half_lam = T(0.5) * lam;
@@ -1002,8 +1013,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T F[5];
                         roe_solve<MODE, OOL>(L, R, kc, F, st);
                         fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
-                        if (gff && (k == 0 || k == 16)) {
-                            T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j0 * 16 + i0;
+                        const int pz = flux_plane(2, k, kc.flux9);
+                        if (gff && pz >= 0) {
+                            T* dst = gff + pz * kFluxPlane + j0 * 16 + i0;
 #pragma unroll
                             for (int q = 0; q < 5; ++q) dst[q * 256] = fz0[q];
                         }
@@ -1014,8 +1026,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T F[5];
                         roe_solve<MODE, OOL>(L, R, kc, F, st);
                         fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
-                        if (gff && (k == 0 || k == 16)) {
-                            T* dst = gff + (k == 0 ? 4 : 5) * 1280 + j1 * 16 + i0;
+                        const int pz = flux_plane(2, k, kc.flux9);
+                        if (gff && pz >= 0) {
+                            T* dst = gff + pz * kFluxPlane + j1 * 16 + i0;
 #pragma unroll
                             for (int q = 0; q < 5; ++q) dst[q * 256] = fz1[q];
                         }
@@ -1069,10 +1082,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         S.fxy[c2 * kFluxStride + wr] = F[2];
                         S.fxy[c3 * kFluxStride + wr] = F[3];
                         S.fxy[4 * kFluxStride + wr] = F[4];
-                        if (gff && (b == 0 || b == 16)) {
-                            // faces -x,+x: [v][k][j];  -y,+y: [v][k][i]
-                            const int face = (isy ? 2 : 0) + (b == 16 ? 1 : 0);
-                            T* dst = gff + face * 1280 + k * 16 + a;
+                        const int face = flux_plane(isy ? 1 : 0, b, kc.flux9);
+                        if (gff && face >= 0) {
+                            // x planes: [v][k][j];  y planes: [v][k][i]
+                            T* dst = gff + face * kFluxPlane + k * 16 + a;
                             dst[0] = F[0];
                             dst[c1 * 256] = F[1];
                             dst[c2 * 256] = F[2];

@@ -32,7 +32,8 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         return GAMER_E_ALIGN;
     const size_t nin = size_t(N) * (SRC == 0 ? 40000 : 20480) * sizeof(T);
     const size_t nout = size_t(N) * 20480 * sizeof(T);
-    const size_t nff = face_flux ? size_t(N) * 7680 * sizeof(T) : 0;
+    const size_t nff =
+        face_flux ? size_t(N) * (p->flux_layout ? 9 : 6) * 1280 * sizeof(T) : 0;
     const size_t nst = status ? size_t(N) * 4 : 0, npa = partials ? size_t(N) * 48 : 0;
     const void* ins[3] = {in, dt, dh};
     const size_t insz[3] = {nin, size_t(N) * 8, size_t(N) * 8};
@@ -53,6 +54,7 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     kc.gm1p = P(p->gamma - 1.0);
     kc.limiter = p->limiter;
     kc.pfb = p->predictor_fallback;
+    kc.flux9 = p->flux_layout;
     kc.floors = (p->rho_floor > 0.0 ? 1 : 0) | (p->p_floor > 0.0 ? 2 : 0);
     kc.rho_floor = T(p->rho_floor);
     kc.p_floor = T(p->p_floor);

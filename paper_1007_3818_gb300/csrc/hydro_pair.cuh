@@ -42,7 +42,7 @@ struct ItemDesc {
     int lo, hi, wr, c1, c2, c3, face, foff;
 };
 
-__device__ __forceinline__ ItemDesc item_desc(int it, int k) {
+__device__ __forceinline__ ItemDesc item_desc(int it, int k, int flux9) {
     constexpr int A = 5 * kFaceStride;  // one face-state array
     ItemDesc d;
     if (it < 256) {
@@ -53,7 +53,7 @@ __device__ __forceinline__ ItemDesc item_desc(int it, int k) {
         d.c1 = 3;
         d.c2 = 1;
         d.c3 = 2;
-        d.face = (k == 0) ? 4 : (k == 16) ? 5 : -1;
+        d.face = flux_plane(2, k, flux9);
         d.foff = frow(it >> 4) * 16 + (it & 15);  // [j][i]
     } else if (it < 256 + 272) {
         // x face f of row j (between i = f-1 and f)
@@ -65,7 +65,7 @@ __device__ __forceinline__ ItemDesc item_desc(int it, int k) {
         d.c1 = 1;
         d.c2 = 2;
         d.c3 = 3;
-        d.face = (f == 0) ? 0 : (f == 16) ? 1 : -1;
+        d.face = flux_plane(0, f, flux9);
         d.foff = k * 16 + j;  // [k][j]
     } else {
         // y face f of column i (between j = f-1 and f)
@@ -76,7 +76,7 @@ __device__ __forceinline__ ItemDesc item_desc(int it, int k) {
         d.c1 = 2;
         d.c2 = 3;
         d.c3 = 1;
-        d.face = (f == 0) ? 2 : (f == 16) ? 3 : -1;
+        d.face = flux_plane(1, f, flux9);
         d.foff = k * 16 + i;  // [k][i]
     }
     return d;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void item_store(T* flux, T* gff, const ItemDesc& d, c
     flux[d.wr + d.c3 * kOutStride] = F[3];
     flux[d.wr + 4 * kOutStride] = F[4];
     if (gff && d.face >= 0) {
-        T* dst = gff + d.face * 1280 + d.foff;
+        T* dst = gff + d.face * kFluxPlane + d.foff;
         dst[0] = F[0];
         dst[d.c1 * 256] = F[1];
         dst[d.c2 * 256] = F[2];
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(kThreads, MINB)
     SmemPair<T>& S = *reinterpret_cast<SmemPair<T>*>(smem_bytes);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int A = 5 * kFaceStride;
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], 1);
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
         const T* gin = in + g * 40000;
         T* gout = out + g * 20480;
-        T* gff = face_flux ? face_flux + g * 7680 : nullptr;
+        T* gff = face_flux ? face_flux + g * (kc.flux9 ? 9 : 6) * kFluxPlane : nullptr;
         const double dtg = dt[g], dhg = dh[g];
         const T lam = static_cast<T>(dtg / dhg);
         const T half_lam = T(0.5) * lam;
@@ -319,7 +318,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         const bool va = (ia < 256) ? (k >= 0) : inner;
                         const bool vb = (r + 1 < 5) && ((ib < 256) ? (k >= 0) : inner);
                         if (va && vb) {
-                            const ItemDesc da = item_desc(ia, k), db = item_desc(ib, k);
+                            const ItemDesc da = item_desc(ia, k, kc.flux9),
+                                           db = item_desc(ib, k, kc.flux9);
                             T La[5], Ra[5], Lb[5], Rb[5], Fa[5], Fb[5];
                             item_load(FS, da, La, Ra);
                             item_load(FS, db, Lb, Rb);
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                             item_store(S.flux, gff, da, Fa);
                             item_store(S.flux, gff, db, Fb);
                         } else if (va) {
-                            const ItemDesc da = item_desc(ia, k);
+                            const ItemDesc da = item_desc(ia, k, kc.flux9);
                             T La[5], Ra[5], Fa[5];
                             item_load(FS, da, La, Ra);
                             if (roe_main<MODE>(La, Ra, kc, Fa)) hlle_apply<MODE>(La, Ra, kc, Fa, st);

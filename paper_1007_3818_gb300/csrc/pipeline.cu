@@ -118,7 +118,7 @@ extern "C" int gamer_pipeline_create(int32_t mode, int64_t batch_groups, int32_t
         if (!ok) break;
         ok = cudaMalloc(&b.in, B * 40000 * pl->esz) == cudaSuccess &&
              cudaMalloc(&b.out, B * 20480 * pl->esz) == cudaSuccess &&
-             (!pl->with_flux || cudaMalloc(&b.ff, B * 7680 * pl->esz) == cudaSuccess) &&
+             (!pl->with_flux || cudaMalloc(&b.ff, B * 9 * 1280 * pl->esz) == cudaSuccess) &&
              cudaMalloc(&b.dt, B * 8) == cudaSuccess && cudaMalloc(&b.dh, B * 8) == cudaSuccess &&
              cudaMalloc(&b.status, B * 4) == cudaSuccess &&
              cudaMalloc(&b.partials, B * 48) == cudaSuccess &&
@@ -160,6 +160,7 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return GAMER_E_DEVICE;
     const size_t e = pl->esz;
+    const size_t ffg = size_t(p->flux_layout ? 9 : 6) * 1280;  // face-flux values per group
     const char* hin = static_cast<const char*>(in_host);
     char* hout = static_cast<char*>(out_host);
     char* hff = static_cast<char*>(face_flux_host);
@@ -196,7 +197,7 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
              cudaMemcpyAsync(hout + size_t(g0) * 20480 * e, S.out, size_t(n) * 20480 * e,
                              cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
         if (ok && ff)
-            ok = cudaMemcpyAsync(hff + size_t(g0) * 7680 * e, S.ff, size_t(n) * 7680 * e,
+            ok = cudaMemcpyAsync(hff + size_t(g0) * ffg * e, S.ff, size_t(n) * ffg * e,
                                  cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
         if (ok && status_host)
             ok = cudaMemcpyAsync(status_host + g0, S.status, size_t(n) * 4,

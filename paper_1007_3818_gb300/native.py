@@ -33,13 +33,17 @@ class GamerError(RuntimeError):
 class gh_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("limiter", ctypes.c_int32), ("predictor_fallback", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2), ("rho_floor", ctypes.c_double),
-                ("p_floor", ctypes.c_double)]
+                ("flux_layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
 
 
-def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0, rho_floor=0.0, p_floor=0.0):
-    return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback), (0, 0),
-                     float(rho_floor), float(p_floor))
+FLUX_PLANES = {0: 6, 1: 9}  # face-flux planes per group by gh_params.flux_layout
+
+
+def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0, rho_floor=0.0, p_floor=0.0,
+                flux_layout=0):
+    return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback),
+                     int(flux_layout), 0, float(rho_floor), float(p_floor))
 
 
 def lib():
@@ -66,6 +70,14 @@ def lib():
         for name in ("gamer_fill_ghosts_uniform_f32", "gamer_fill_ghosts_uniform_f64"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, i32, i32, i32, i32, vp]
+            f.restype = ctypes.c_int
+        for name in ("gamer_flux_fixup_f32", "gamer_flux_fixup_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, vp, i32, vp, vp, i64, i64, vp, i64, vp, vp]
+            f.restype = ctypes.c_int
+        for name in ("gamer_restrict_f32", "gamer_restrict_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, i64, i64, vp, i64, vp, vp]
             f.restype = ctypes.c_int
         L.gamer_hydro_dt_workspace_bytes.argtypes = [i64, i32]
         L.gamer_hydro_dt_workspace_bytes.restype = ctypes.c_size_t
@@ -155,7 +167,8 @@ def _advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream
     T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
     N = int(inp.shape[0])
     args = [_ptr(inp, T, (5, 20, 20, 20), "in"), _ptr(out, T, (5, 16, 16, 16), "out"),
-            _ptr(face_flux, T, (6, 5, 16, 16), "face_flux"), _ptr(dt, torch.float64, (), "dt"),
+            _ptr(face_flux, T, (FLUX_PLANES[params.flux_layout], 5, 16, 16), "face_flux"),
+            _ptr(dt, torch.float64, (), "dt"),
             _ptr(dh, torch.float64, (), "dh"), _ptr(status, torch.int32, (), "status"),
             _ptr(partials, torch.float64, (6,), "partials")]
     for t, nm in ((out, "out"), (face_flux, "face_flux"), (dt, "dt"), (dh, "dh"),
@@ -206,7 +219,8 @@ def hydro_advance_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, sta
         if t is not None and int(t.shape[0]) != G:
             raise GamerError(-2, f"{nm} must hold gx*gy*gz = {G} groups")
     args = [_ptr(level, T, (5, 16, 16, 16), "level"), _ptr(out, T, (5, 16, 16, 16), "out"),
-            _ptr(face_flux, T, (6, 5, 16, 16), "face_flux"), int(gx), int(gy), int(gz), int(bc),
+            _ptr(face_flux, T, (FLUX_PLANES[params.flux_layout], 5, 16, 16), "face_flux"),
+            int(gx), int(gy), int(gz), int(bc),
             _ptr(dt, torch.float64, (), "dt"), _ptr(dh, torch.float64, (), "dh"),
             _ptr(status, torch.int32, (), "status"), _ptr(partials, torch.float64, (6,), "partials")]
     rc = getattr(lib(), _ADV_LEVEL[mode])(*args, ctypes.byref(params), _stream(stream))
@@ -248,6 +262,72 @@ def gamer_fill_ghosts_uniform_f32(level, inp, gx, gy, gz, bc, stream=None):
 def gamer_fill_ghosts_uniform_f64(level, inp, gx, gy, gz, bc, stream=None):
     import torch
     _fill("gamer_fill_ghosts_uniform_f64", torch.float64, level, inp, gx, gy, gz, bc, stream)
+
+
+# Records of the coarse-fine coupling (layouts of gamer_cf_face and
+# gamer_cf_child): numpy structured arrays, moved to the device as bytes.
+CF_FACE_FIELDS = ("coarse", "fine", "dir", "plane", "side", "quadrant")
+CF_CHILD_FIELDS = ("coarse", "fine", "octant", "reserved")
+
+
+def records_to_device(records, fields, itemsize, device="cuda"):
+    """Copy a numpy structured array of coarse-fine records to a device byte
+    tensor (the C structs' layout: int64 indices, then int32 fields)."""
+    import numpy as np
+    import torch
+    a = np.ascontiguousarray(records)
+    if a.dtype.names != fields or a.dtype.itemsize != itemsize:
+        raise GamerError(-2, f"records must have fields {fields} ({itemsize} bytes each)")
+    raw = np.frombuffer(a.tobytes(), dtype=np.uint8).copy()
+    return torch.from_numpy(raw).to(device)
+
+
+def _bytes_ptr(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise GamerError(-1, f"{name} must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def flux_fixup(mode, coarse, coarse_flux, fine_flux, dt, dh, faces, bad=None, stream=None):
+    """Coarse-fine flux fix-up in place on coarse [Nc,5,16,16,16]:
+    coarse_flux [Nc,9,5,16,16] (nine-plane layout), fine_flux
+    [n_sub,Nf,6,5,16,16], dt/dh [Nc] f64, faces: device bytes of gamer_cf_face
+    records (records_to_device), bad: int32 [1] device counter or None."""
+    import torch
+    T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+    Nc = int(coarse.shape[0])
+    if fine_flux.dim() != 6 or tuple(fine_flux.shape[2:]) != (6, 5, 16, 16):
+        raise GamerError(-2, "fine_flux must be [n_sub, Nf, 6, 5, 16, 16]")
+    n_sub, Nf = int(fine_flux.shape[0]), int(fine_flux.shape[1])
+    if int(coarse_flux.shape[0]) != Nc or int(dt.shape[0]) != Nc or int(dh.shape[0]) != Nc:
+        raise GamerError(-2, "coarse_flux, dt and dh must hold Nc groups")
+    if faces.numel() % 32:
+        raise GamerError(-2, "faces must hold whole 32-byte records")
+    name = "gamer_flux_fixup_f64" if mode == GAMER_MODE_F64 else "gamer_flux_fixup_f32"
+    rc = getattr(lib(), name)(
+        _ptr(coarse, T, (5, 16, 16, 16), "coarse"), _ptr(coarse_flux, T, (9, 5, 16, 16),
+                                                        "coarse_flux"),
+        _ptr(fine_flux, T, None, "fine_flux"), n_sub, _ptr(dt, torch.float64, (), "dt"),
+        _ptr(dh, torch.float64, (), "dh"), Nc, Nf, _bytes_ptr(faces, "faces"),
+        faces.numel() // 32, _ptr(bad, torch.int32, (), "bad"), _stream(stream))
+    _check(rc, name)
+
+
+def restrict(mode, fine, coarse, children, bad=None, stream=None):
+    """Restriction of fine [Nf,5,16,16,16] onto the covered octants of coarse
+    [Nc,5,16,16,16]; children: device bytes of gamer_cf_child records."""
+    import torch
+    T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+    if children.numel() % 24:
+        raise GamerError(-2, "children must hold whole 24-byte records")
+    name = "gamer_restrict_f64" if mode == GAMER_MODE_F64 else "gamer_restrict_f32"
+    rc = getattr(lib(), name)(
+        _ptr(fine, T, (5, 16, 16, 16), "fine"), _ptr(coarse, T, (5, 16, 16, 16), "coarse"),
+        int(coarse.shape[0]), int(fine.shape[0]), _bytes_ptr(children, "children"),
+        children.numel() // 24, _ptr(bad, torch.int32, (), "bad"), _stream(stream))
+    _check(rc, name)
 
 
 def gamer_hydro_dt_workspace_bytes(N, n_levels):

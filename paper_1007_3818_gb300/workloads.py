@@ -289,3 +289,85 @@ def amr_batch_parts(counts=(2000, 12000, 40000), seed=DEFAULT_SEED, gamma=5.0 / 
     origins = rng.integers(0, base_n, size=(level.shape[0], 3))
     dh_level = np.array([dh0 / (2 ** l) for l in range(len(counts))])
     return base, origins, level, dh_level
+
+
+# --------------------------------------------------------------------------
+# Two-level (refinement ratio 2) bookkeeping for the coarse-fine coupling:
+# which fine patch group covers which coarse octant, and where the interfaces
+# between refined and unrefined coarse patches lie.  Index arithmetic and
+# copies only.
+
+# one interface record: 8x8 coarse faces of one coarse group's flux plane
+# covered by one face of one fine group (layout of gamer_cf_face)
+CF_FACE_DTYPE = np.dtype([("coarse", "<i8"), ("fine", "<i8"), ("dir", "<i4"), ("plane", "<i4"),
+                          ("side", "<i4"), ("quadrant", "<i4")])
+# one child record: the fine group covering one octant of a coarse group
+# (layout of gamer_cf_child)
+CF_CHILD_DTYPE = np.dtype([("coarse", "<i8"), ("fine", "<i8"), ("octant", "<i4"),
+                           ("reserved", "<i4")])
+
+
+def cf_records(cg, refined):
+    """Records of a periodic coarse level of cg = (cgx, cgy, cgz) groups whose
+    coarse patches (8^3-cell octants, integer coords in [0, 2*cg)) listed in
+    `refined` are each covered by one fine group (fine id = list position).
+
+    Returns (children, faces): CF_CHILD_DTYPE and CF_FACE_DTYPE arrays.  A face
+    record is made for every fine-group face whose neighbouring coarse patch is
+    not refined; the corrected coarse cells are that patch's layer next to it."""
+    cg = tuple(int(c) for c in cg)
+    refined = [tuple(int(v) for v in p) for p in refined]
+    index = {p: f for f, p in enumerate(refined)}
+    children = np.zeros(len(refined), dtype=CF_CHILD_DTYPE)
+    faces = []
+
+    def group_of(p):
+        g = [p[d] // 2 for d in range(3)]
+        return (g[2] * cg[1] + g[1]) * cg[0] + g[0]
+
+    for f, p in enumerate(refined):
+        children[f] = (group_of(p), f, (p[0] & 1) | ((p[1] & 1) << 1) | ((p[2] & 1) << 2), 0)
+        for d in range(3):
+            for s in (-1, 1):
+                q = list(p)
+                q[d] = (q[d] + s) % (2 * cg[d])
+                q = tuple(q)
+                if q in index:
+                    continue
+                # the fine region lies on the + side of patch q when s = -1
+                side = 1 if s == -1 else 0
+                low = q[d] & 1          # position of patch q in its group along d
+                plane = (low + 1) if side == 1 else low
+                # in-plane octant bits of patch q: [a][b] = [k][j], [k][i], [j][i]
+                ta, tb = {0: (2, 1), 1: (2, 0), 2: (1, 0)}[d]
+                quadrant = (q[ta] & 1) | ((q[tb] & 1) << 1)
+                faces.append((group_of(q), f, d, plane, side, quadrant))
+    return children, np.array(faces, dtype=CF_FACE_DTYPE)
+
+
+def composite_fine_level(coarse_groups, cg, fine_groups, refined):
+    """Fine-resolution copy [5][2*16*cgz][2*16*cgy][2*16*cgx] of a two-level
+    state: every coarse cell injected into its 2x2x2 fine cells, then the fine
+    groups written over the patches they cover."""
+    cgx, cgy, cgz = cg
+    U = groups_to_level(coarse_groups, cgx, cgy, cgz)
+    F = U.repeat(2, axis=1).repeat(2, axis=2).repeat(2, axis=3)
+    for f, p in enumerate(refined):
+        x0, y0, z0 = 16 * p[0], 16 * p[1], 16 * p[2]
+        F[:, z0:z0 + 16, y0:y0 + 16, x0:x0 + 16] = fine_groups[f]
+    return F
+
+
+def fine_tiles(coarse_groups, cg, fine_groups, refined):
+    """Ghost-padded 20^3 tiles of the fine groups, ghosts taken (periodically)
+    from the composite fine-resolution state: neighbouring fine groups where
+    refined, injected coarse cells elsewhere."""
+    F = composite_fine_level(coarse_groups, cg, fine_groups, refined)
+    nz, ny, nx = F.shape[1:]
+    out = np.empty((len(refined), 5, 20, 20, 20), dtype=F.dtype)
+    for f, p in enumerate(refined):
+        zi = (16 * p[2] - 2 + np.arange(20)) % nz
+        yi = (16 * p[1] - 2 + np.arange(20)) % ny
+        xi = (16 * p[0] - 2 + np.arange(20)) % nx
+        out[f] = F[:, zi][:, :, yi][:, :, :, xi]
+    return out

@@ -78,8 +78,9 @@ def test_advance_rejects_bad_arguments(lib, name):
     assert _adv(lib, name, params=native.make_params(1.4, limiter=3)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, predictor_fallback=2)) == -2
     bad = native.make_params(1.4)
-    bad.reserved[0] = 1
+    bad.reserved = 1
     assert _adv(lib, name, params=bad) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, flux_layout=2)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, rho_floor=-1e-3)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, p_floor=float("nan"))) == -2
     assert _adv(lib, name, params=native.make_params(1.4, p_floor=float("inf"))) == -2
@@ -111,6 +112,32 @@ def test_advance_level_rejects_bad_arguments(lib, name):
     assert call(level=None) == -1
     assert call(level=FAKE + 8) == -3                 # level needs 16 B alignment
     assert call(out=FAKE + 4096) == -6                # out inside the level
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_flux_fixup_and_restrict_reject_bad_arguments(lib, prec):
+    fix = getattr(lib, f"gamer_flux_fixup_{prec}")
+    res = getattr(lib, f"gamer_restrict_{prec}")
+    GB = 1 << 32
+
+    def call_fix(coarse=FAKE, cflux=FAKE + GB, fflux=FAKE + 2 * GB, n_sub=2, dt=FAKE + 3 * GB,
+                 faces=FAKE + 4 * GB, n=5, bad=None):
+        return fix(P(coarse) if coarse else None, P(cflux), P(fflux), n_sub, P(dt),
+                   P(FAKE + 5 * GB), 8, 4, P(faces) if faces else None, n,
+                   P(bad) if bad else None, None)
+
+    assert call_fix(n=0) == 0                       # no records: no-op
+    assert call_fix(n_sub=0) == -2
+    assert call_fix(n=-1) == -2
+    assert call_fix(coarse=None) == -1
+    assert call_fix(faces=None) == -1
+    assert call_fix(faces=FAKE + 4 * GB + 4) == -3   # records need 8-byte alignment
+    assert call_fix(bad=FAKE + 6 * GB + 2) == -3
+    assert call_fix(cflux=FAKE + 64) == -6           # coarse state overlaps its fluxes
+    assert res(P(FAKE), P(FAKE + GB), 8, 4, P(FAKE + 2 * GB), 0, None, None) == 0
+    assert res(P(FAKE), P(FAKE + GB), -1, 4, P(FAKE + 2 * GB), 3, None, None) == -2
+    assert res(None, P(FAKE + GB), 8, 4, P(FAKE + 2 * GB), 3, None, None) == -1
+    assert res(P(FAKE), P(FAKE + 128), 8, 4, P(FAKE + 2 * GB), 3, None, None) == -6
 
 
 def test_fill_ghosts_rejects_bad_arguments(lib):
