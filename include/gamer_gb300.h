@@ -71,7 +71,9 @@ typedef struct gh_params {
                                    direction at 0, 8 and 16 cells (x: 0,1,2; y: 3,4,5;
                                    z: 6,7,8), which adds the patch boundaries inside the
                                    group for the coarse-fine flux fix-up                   */
-    int32_t reserved;           /* must be 0                                                */
+    int32_t riemann;            /* Riemann solver: 0 Roe with Harten-Hyman entropy fix and
+                                   HLLE fallback (default; the paper's), 1 HLLC (a scheme
+                                   variant: exact on isolated contact and shear waves)     */
     double rho_floor;           /* finite, >= 0; 0 = off (default): an updated density below
                                    it is raised to it, momentum kept                         */
     double p_floor;             /* finite, >= 0; 0 = off (default): where the updated density

@@ -87,6 +87,7 @@ struct Scheme {
     R rho_floor = R(0.0);  // 0: off
     R p_floor = R(0.0);    // 0: off
     int flux_layout = 0;   // 0: six box faces, 1: nine planes
+    int solver = 0;        // Riemann solver: 0 Roe (with HLLE fallback), 1 HLLC
 
     // Conserved -> primitive.  p = (gamma-1) (E - 0.5 |m|^2 / rho).
     void prim(const R U[5], R W[5]) const {
@@ -248,6 +249,72 @@ struct Scheme {
         for (int i = 0; i < 5; ++i) F[i] = R(0.5) * (FL[i] + FR[i]) - R(0.5) * Du[i];
         return false;
     }
+
+    // READING R20 (scheme variant): HLLC flux through a face normal to
+    // direction d (Toro 2009, Sec. 10.4).  Wave-speed bounds as the HLLE of
+    // R7 (Einfeldt's with the Roe speeds, Davis's when c~^2 <= 0); contact
+    // speed S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R)) /
+    // (rho_L (S_L - u_L) - rho_R (S_R - u_R)); star states
+    // U*_K = rho_K (S_K - u_K) / (S_K - S*) (1, S*, v_K, w_K,
+    // E_K / rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))); the flux is
+    // F_L, F_L + S_L (U*_L - U_L), F_R + S_R (U*_R - U_R) or F_R by where the
+    // face lies in the fan.
+    void hllc(int d, const R UL[5], const R UR[5], R F[5]) const {
+        R WL[5], WR[5], FL[5], FR[5];
+        prim(UL, WL);
+        prim(UR, WR);
+        flux(d, WL, UL[4], FL);
+        flux(d, WR, UR[4], FR);
+        const int n = 1 + d, t1 = 1 + (d + 1) % 3, t2 = 1 + (d + 2) % 3;
+        R cL = r_sqrt(gamma * WL[4] / WL[0]);
+        R cR = r_sqrt(gamma * WR[4] / WR[0]);
+        R rr = r_sqrt(WR[0] / WL[0]);
+        R uT = (WL[n] + rr * WR[n]) / (R(1.0) + rr);
+        R vT = (WL[t1] + rr * WR[t1]) / (R(1.0) + rr);
+        R wT = (WL[t2] + rr * WR[t2]) / (R(1.0) + rr);
+        R HT = ((UL[4] + WL[4]) / WL[0] + rr * (UR[4] + WR[4]) / WR[0]) / (R(1.0) + rr);
+        R cT2 = gm1 * (HT - R(0.5) * (uT * uT + vT * vT + wT * wT));
+        R sl = WL[n] - cL, sr = WR[n] + cR;
+        if (cT2 > R(0.0)) {
+            sl = r_min(sl, uT - r_sqrt(cT2));
+            sr = r_max(sr, uT + r_sqrt(cT2));
+        } else {
+            sl = r_min(sl, WR[n] - cR);
+            sr = r_max(sr, WL[n] + cL);
+        }
+        R ss = (WR[4] - WL[4] + WL[0] * WL[n] * (sl - WL[n]) - WR[0] * WR[n] * (sr - WR[n])) /
+               (WL[0] * (sl - WL[n]) - WR[0] * (sr - WR[n]));
+        if (sl >= R(0.0)) {
+            for (int i = 0; i < 5; ++i) F[i] = FL[i];
+            return;
+        }
+        if (sr <= R(0.0)) {
+            for (int i = 0; i < 5; ++i) F[i] = FR[i];
+            return;
+        }
+        const bool left = ss >= R(0.0);
+        const R* U = left ? UL : UR;
+        const R* W = left ? WL : WR;
+        const R* FK = left ? FL : FR;
+        const R sK = left ? sl : sr;
+        const R fac = W[0] * (sK - W[n]) / (sK - ss);
+        R Us[5];
+        Us[0] = fac;
+        Us[n] = fac * ss;
+        Us[t1] = fac * W[t1];
+        Us[t2] = fac * W[t2];
+        Us[4] = fac * (U[4] / W[0] + (ss - W[n]) * (ss + W[4] / (W[0] * (sK - W[n]))));
+        for (int i = 0; i < 5; ++i) F[i] = FK[i] + sK * (Us[i] - U[i]);
+    }
+
+    // The Riemann flux of the configured solver; true when Roe fell back to HLLE.
+    bool riemann(int d, const R UL[5], const R UR[5], R F[5]) const {
+        if (solver == 1) {
+            hllc(d, UL, UR, F);
+            return false;
+        }
+        return roe(d, UL, UR, true, F);
+    }
 };
 
 // cells of a padded box that the step reads (see READING on corner ghosts):
@@ -358,7 +425,7 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
             for (int f = 0; f <= nx; ++f) {
                 const R* L = &Uh[qidx(f - 1, j, k) * 30 + 1 * 5];  // x+ face of left cell
                 const R* Rr = &Uh[qidx(f, j, k) * 30 + 0 * 5];     // x- face of right cell
-                if (S.roe(0, L, Rr, true, &Fx[(((std::size_t)k * ny + j) * (nx + 1) + f) * 5]))
+                if (S.riemann(0, L, Rr, &Fx[(((std::size_t)k * ny + j) * (nx + 1) + f) * 5]))
                     st |= ORACLE_ST_HLLE_FALLBACK;
             }
     for (int k = 0; k < nz; ++k)
@@ -366,7 +433,7 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
             for (int i = 0; i < nx; ++i) {
                 const R* L = &Uh[qidx(i, f - 1, k) * 30 + 3 * 5];
                 const R* Rr = &Uh[qidx(i, f, k) * 30 + 2 * 5];
-                if (S.roe(1, L, Rr, true, &Fy[(((std::size_t)k * (ny + 1) + f) * nx + i) * 5]))
+                if (S.riemann(1, L, Rr, &Fy[(((std::size_t)k * (ny + 1) + f) * nx + i) * 5]))
                     st |= ORACLE_ST_HLLE_FALLBACK;
             }
     for (int f = 0; f <= nz; ++f)
@@ -374,7 +441,7 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
             for (int i = 0; i < nx; ++i) {
                 const R* L = &Uh[qidx(i, j, f - 1) * 30 + 5 * 5];
                 const R* Rr = &Uh[qidx(i, j, f) * 30 + 4 * 5];
-                if (S.roe(2, L, Rr, true, &Fz[(((std::size_t)f * ny + j) * nx + i) * 5]))
+                if (S.riemann(2, L, Rr, &Fz[(((std::size_t)f * ny + j) * nx + i) * 5]))
                     st |= ORACLE_ST_HLLE_FALLBACK;
             }
     auto FX = [&](int f, int j, int k) { return &Fx[(((std::size_t)k * ny + j) * (nx + 1) + f) * 5]; };
@@ -480,6 +547,7 @@ Scheme<R> make_scheme(const oracle_params* p) {
     S.rho_floor = R(p->rho_floor);
     S.p_floor = R(p->p_floor);
     S.flux_layout = p->flux_layout;
+    S.solver = p->riemann;
     return S;
 }
 
@@ -487,7 +555,8 @@ bool params_ok(const oracle_params* p) {
     return p && std::isfinite(p->gamma) && p->gamma > 1.0 && p->limiter >= 0 && p->limiter <= 2 &&
            (p->predictor_fallback == 0 || p->predictor_fallback == 1) &&
            std::isfinite(p->rho_floor) && p->rho_floor >= 0.0 && std::isfinite(p->p_floor) &&
-           p->p_floor >= 0.0 && (p->flux_layout == 0 || p->flux_layout == 1);
+           p->p_floor >= 0.0 && (p->flux_layout == 0 || p->flux_layout == 1) &&
+           (p->riemann == 0 || p->riemann == 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -609,6 +678,13 @@ int oracle_roe_flux(int dir, const double UL[5], const double UR[5], double gamm
     oracle_params p = {gamma, 0, 0};
     return make_scheme<double>(&p).roe(dir, UL, UR, entropy_fix != 0, F) ? 1 : 0;
 }
+void oracle_hllc_flux(int dir, const double UL[5], const double UR[5], double gamma, double F[5]) {
+    oracle_params p = {gamma, 0, 0};
+    p.riemann = 1;
+    Scheme<double> S = make_scheme<double>(&p);
+    S.hllc(dir, UL, UR, F);
+}
+
 void oracle_hlle_flux(int dir, const double UL[5], const double UR[5], double gamma, double F[5]) {
     oracle_params p = {gamma, 0, 0};
     Scheme<double> S = make_scheme<double>(&p);

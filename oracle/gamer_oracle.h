@@ -38,6 +38,7 @@ typedef struct {
     double p_floor;          /* >= 0; 0 = off: updated p below it is raised to it   */
     int32_t flux_layout;     /* 0: six box faces; 1: nine planes, three per direction
                                 at 0, n/2 and n cells (n even)                       */
+    int32_t riemann;         /* 0: Roe with HLLE fallback (the paper's); 1: HLLC     */
 } oracle_params;
 
 /* status bits (per box / per group) */
@@ -122,6 +123,8 @@ void oracle_prim_from_cons(const double U[5], double gamma, double W[5]);
 void oracle_cons_from_prim(const double W[5], double gamma, double U[5]);
 void oracle_euler_flux(int dir, const double W[5], double E, double F[5]);
 double oracle_limiter(int id, double a, double b);
+/* HLLC flux (scheme variant) in direction dir from conserved L/R states. */
+void oracle_hllc_flux(int dir, const double UL[5], const double UR[5], double gamma, double F[5]);
 /* Roe flux in direction dir from conserved L/R states; returns 1 when the HLLE
  * fallback replaced it, else 0.  entropy_fix = 0 switches the fix off (pins). */
 int oracle_roe_flux(int dir, const double UL[5], const double UR[5], double gamma,

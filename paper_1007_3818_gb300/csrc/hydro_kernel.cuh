@@ -405,8 +405,56 @@ __device__ __noinline__ RoeIO<T> roe_call(RoeIO<T> L, RoeIO<T> R, KConst<T, P> k
     return out;
 }
 
-// Riemann solve through the inline or the out-of-line solver (OOL = 1).
-template <int OOL> struct RoeTag {};
+// HLLC flux (Toro 2009, Sec. 10.4) in the rotated frame, with the wave-speed
+// bounds of the HLLE fallback: Einfeldt's (u_L - c_L, u~ - c~ / u_R + c_R,
+// u~ + c~) when c~^2 > 0, Davis's over both states otherwise.  The contact
+// speed S* from the two momentum balances; the star state of the side that
+// holds the face.  Never falls back.
+template <int MODE, class T, class P>
+__device__ __forceinline__ void hllc_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                         T F[5]) {
+    const T irL = rcp_(L[0]), irR = rcp_(R[0]);
+    const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
+    const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
+    const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
+    const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
+    const T cL = sqrt_(kc.gamma * pL * irL);
+    const T cR = sqrt_(kc.gamma * pR * irR);
+    const T rr = sqrt_(R[0] * irL);
+    const T i1 = rcp_(T(1) + rr);
+    const T uT = (uL + rr * uR) * i1, vT = (vL + rr * vR) * i1, wT = (wL + rr * wR) * i1;
+    const T HT = ((L[4] + pL) * irL + rr * ((R[4] + pR) * irR)) * i1;
+    const T cT2 = kc.gm1 * (HT - T(0.5) * (uT * uT + vT * vT + wT * wT));
+    T sl = uL - cL, sr = uR + cR;
+    if (cT2 > T(0)) {
+        const T cT = sqrt_(cT2);
+        sl = min_(sl, uT - cT);
+        sr = max_(sr, uT + cT);
+    } else {
+        sl = min_(sl, uR - cR);
+        sr = max_(sr, uL + cL);
+    }
+    const T mL = L[0] * (sl - uL), mR = R[0] * (sr - uR);
+    const T ss = (pR - pL + mL * uL - mR * uR) * rcp_(mL - mR);
+    // upwind side K: left when the face sees S_L >= 0 or the left star region
+    const bool left = ss >= T(0);
+    const T* U = left ? L : R;
+    const T uK = left ? uL : uR, vK = left ? vL : vR, wK = left ? wL : wR;
+    const T pK = left ? pL : pR, irK = left ? irL : irR;
+    const T sK = left ? sl : sr, mK = left ? mL : mR;
+    const T FK[5] = {U[1], U[1] * uK + pK, U[1] * vK, U[1] * wK, (U[4] + pK) * uK};
+    // S_K (U*_K - U_K), or 0 outside the fan (the plain upwind flux)
+    const bool fan = left ? (sl < T(0)) : (sr > T(0));
+    const T fac = mK * rcp_(sK - ss);   // rho_K (S_K - u_K) / (S_K - S*)
+    const T Us[5] = {fac, fac * ss, fac * vK, fac * wK,
+                     fac * (U[4] * irK + (ss - uK) * (ss + pK * rcp_(mK)))};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = fan ? FK[q] + sK * (Us[q] - U[q]) : FK[q];
+}
+
+// Riemann solve by variant: 0 Roe inline, 1 Roe through one out-of-line
+// copy, 2 HLLC inline.
+template <int RSV> struct RoeTag {};
 template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_pick(RoeTag<0>, const T L[5], const T R[5],
                                          const KConst<T, P>& kc, T F[5], uint32_t& st) {
@@ -427,10 +475,15 @@ __device__ __forceinline__ void roe_pick(RoeTag<1>, const T L[5], const T R[5],
     for (int q = 0; q < 5; ++q) F[q] = r.v[q];
     st |= r.st;
 }
-template <int MODE, int OOL, class T, class P>
+template <int MODE, class T, class P>
+__device__ __forceinline__ void roe_pick(RoeTag<2>, const T L[5], const T R[5],
+                                         const KConst<T, P>& kc, T F[5], uint32_t&) {
+    hllc_rot<MODE>(L, R, kc, F);
+}
+template <int MODE, int RSV, class T, class P>
 __device__ __forceinline__ void roe_solve(const T L[5], const T R[5], const KConst<T, P>& kc,
                                           T F[5], uint32_t& st) {
-    roe_pick<MODE>(RoeTag<OOL>(), L, R, kc, F, st);
+    roe_pick<MODE>(RoeTag<RSV>(), L, R, kc, F, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -775,7 +828,7 @@ template <> struct SumAcc<float> {
 // each plane is gathered from the group and its neighbours (fused ghost fill).
 // RING: input planes in flight (2: the copy of plane k+2 goes out after phase A
 // of plane k; 3: plane k+3 does, one full iteration ahead of its use).
-template <int MODE, int MINB, int OOL = 0, int SRC = 0, int RING = 2>
+template <int MODE, int MINB, int RSV = 0, int SRC = 0, int RING = 2>
 __global__ void __launch_bounds__(kThreads, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
@@ -1011,7 +1064,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T L[5] = {zp0[0], zp0[3], zp0[1], zp0[2], zp0[4]};
                         T R[5] = {zm0[0], zm0[3], zm0[1], zm0[2], zm0[4]};
                         T F[5];
-                        roe_solve<MODE, OOL>(L, R, kc, F, st);
+                        roe_solve<MODE, RSV>(L, R, kc, F, st);
                         fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
                         const int pz = flux_plane(2, k, kc.flux9);
                         if (gff && pz >= 0) {
@@ -1024,7 +1077,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T L[5] = {zp1[0], zp1[3], zp1[1], zp1[2], zp1[4]};
                         T R[5] = {zm1[0], zm1[3], zm1[1], zm1[2], zm1[4]};
                         T F[5];
-                        roe_solve<MODE, OOL>(L, R, kc, F, st);
+                        roe_solve<MODE, RSV>(L, R, kc, F, st);
                         fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
                         const int pz = flux_plane(2, k, kc.flux9);
                         if (gff && pz >= 0) {
@@ -1076,7 +1129,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         R[2] = RA[c2 * kFaceStride + hi];
                         R[3] = RA[c3 * kFaceStride + hi];
                         R[4] = RA[4 * kFaceStride + hi];
-                        roe_solve<MODE, OOL>(L, R, kc, F, st);
+                        roe_solve<MODE, RSV>(L, R, kc, F, st);
                         S.fxy[wr] = F[0];
                         S.fxy[c1 * kFluxStride + wr] = F[1];
                         S.fxy[c2 * kFluxStride + wr] = F[2];

@@ -67,9 +67,12 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     // or 2 CTAs/SM, FP64 for 1; 1 (FP32 tiles only) -- the same with the
     // Riemann solver out of line; 2 (tiles only) -- two interleaved problems
     // per thread (pair kernel, 2 CTAs/SM in FP32, 1 in FP64), van Leer limiter
-    // compiled in plus a runtime-limiter build for the others.
+    // compiled in plus a runtime-limiter build for the others.  The HLLC
+    // solver (p->riemann = 1) comes in the default shape only (3 CTAs/SM in
+    // FP32 modes, 1 in FP64) and overrides the variant and CTA settings.
+    const bool hllc = p->riemann == 1;
     if constexpr (SRC == 0) {
-      if (var == 2) {
+      if (var == 2 && !hllc) {
         constexpr int MB = (MODE == GAMER_MODE_F64) ? 1 : 2;
         auto kern = (p->limiter == 0) ? hydro_pair_kernel<MODE, MB, 0>
                                       : hydro_pair_kernel<MODE, MB, -1>;
@@ -109,6 +112,14 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
             if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
         }
     }
+    if (hllc) {
+        if constexpr (MODE == GAMER_MODE_F64) {
+            kern = hydro_step_kernel<MODE, 1, 2, SRC, 3>;
+        } else {
+            kern = hydro_step_kernel<MODE, 3, 2, SRC, 2>;
+            smem = int(sizeof(Smem<T, 2>)) + extra;
+        }
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return GAMER_E_CUDA;
@@ -117,7 +128,7 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
             cudaSuccess ||
         per_sm < 1)
         return GAMER_E_CUDA;
-    if (want > 0 && want < per_sm) per_sm = want;
+    if (want > 0 && want < per_sm && !hllc) per_sm = want;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
     kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh, status,
                                                             partials, N, kc, geo);

@@ -33,7 +33,7 @@ class GamerError(RuntimeError):
 class gh_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("limiter", ctypes.c_int32), ("predictor_fallback", ctypes.c_int32),
-                ("flux_layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("flux_layout", ctypes.c_int32), ("riemann", ctypes.c_int32),
                 ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
 
 
@@ -41,9 +41,9 @@ FLUX_PLANES = {0: 6, 1: 9}  # face-flux planes per group by gh_params.flux_layou
 
 
 def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0, rho_floor=0.0, p_floor=0.0,
-                flux_layout=0):
+                flux_layout=0, riemann=0):
     return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback),
-                     int(flux_layout), 0, float(rho_floor), float(p_floor))
+                     int(flux_layout), int(riemann), float(rho_floor), float(p_floor))
 
 
 def lib():
