@@ -597,11 +597,39 @@ __device__ __forceinline__ bool is_read_cell(int i, int j, int k) {
     return o <= 1 || (o == 2 && ni && nj && nk);
 }
 
-// Conserved plane -> primitive plane (all 400 cells; the flag covers the read cells).
+// Which of this thread's plane cells (c = tid + r * kThreads, r < 3) the
+// stencil reads, for the three kinds of plane (bit 3 * kind + r): kind 0 a
+// plane inside the group, 1 one plane outside (-1, 16), 2 two outside (-2, 17).
+__device__ __forceinline__ uint32_t read_cell_mask() {
+    uint32_t m = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int c = int(threadIdx.x) + r * kThreads;
+        if (c >= kPlane) break;
+        const int i = c % 20 - 2, j = c / 20 - 2;
+        if (is_read_cell(i, j, 0)) m |= 1u << r;
+        if (is_read_cell(i, j, -1)) m |= 1u << (3 + r);
+        if (is_read_cell(i, j, -2)) m |= 1u << (6 + r);
+    }
+    return m;
+}
+
+// the read bits of plane kp out of read_cell_mask()
+__device__ __forceinline__ uint32_t plane_read_bits(uint32_t mask, int kp) {
+    const int kind = ((unsigned)kp < 16u) ? 0 : (kp == -1 || kp == 16) ? 1 : 2;
+    return (mask >> (3 * kind)) & 7u;
+}
+
+// Conserved plane -> primitive plane (all 400 cells; the flag covers the read
+// cells, `rbits` from plane_read_bits).
 template <int MODE, class T, class P>
-__device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W, int kp,
-                                              const KConst<T, P>& kc, uint32_t& st) {
-    for (int c = threadIdx.x; c < kPlane; c += kThreads) {
+__device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W,
+                                              uint32_t rbits, const KConst<T, P>& kc,
+                                              uint32_t& st) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int c = int(threadIdx.x) + r * kThreads;
+        if (c >= kPlane) break;
         T u[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) u[q] = U[q * kPlane + c];
@@ -611,8 +639,7 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
         W[2 * kPlane + c] = u[2] * ir;
         W[3 * kPlane + c] = u[3] * ir;
         W[4 * kPlane + c] = pressure<MODE>(u[0], u[1], u[2], u[3], u[4], ir, kc);
-        const int i = c % 20 - 2, j = c / 20 - 2;
-        if (is_read_cell(i, j, kp)) {
+        if ((rbits >> r) & 1u) {
             bool fin = true;
 #pragma unroll
             for (int q = 0; q < 5; ++q) fin = fin && finite_(u[q]);
@@ -842,6 +869,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     Smem<T, RING>& S = *reinterpret_cast<Smem<T, RING>*>(smem_bytes);
     constexpr int ROFF = raw_offset<SRC, T>();
     GatherPlan* gplan = reinterpret_cast<GatherPlan*>(smem_bytes + sizeof(Smem<T, RING>));
+    const uint32_t rmask = read_cell_mask();
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
@@ -906,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (mbar_wait(&S.mbar[0], parity & 1u)) {
             parity ^= 1u;
             pending &= ~1u;
-            convert_plane<MODE>(S.raw[0] + ROFF, S.W[0], -2, kc, st);
+            convert_plane<MODE>(S.raw[0] + ROFF, S.W[0], plane_read_bits(rmask, -2), kc, st);
         } else {
             timed_out = true;
         }
@@ -918,7 +946,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
-                convert_plane<MODE>(S.raw[s] + ROFF, S.W[kp + 2], kp, kc, st);
+                convert_plane<MODE>(S.raw[s] + ROFF, S.W[kp + 2], plane_read_bits(rmask, kp), kc,
+                                    st);
             } else {
                 timed_out = true;
             }
@@ -1153,7 +1182,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
-                        convert_plane<MODE>(S.raw[slot] + ROFF, S.W[(k + 4) % 3], k + 2, kc, st);
+                        convert_plane<MODE>(S.raw[slot] + ROFF, S.W[(k + 4) % 3],
+                                            plane_read_bits(rmask, k + 2), kc, st);
                     } else {
                         timed_out = true;
                     }

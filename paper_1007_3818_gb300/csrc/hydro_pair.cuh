@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     SmemPair<T>& S = *reinterpret_cast<SmemPair<T>*>(smem_bytes);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t rmask = read_cell_mask();
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) mbar_init(&S.mbar[s], 1);
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (mbar_wait(&S.mbar[0], parity & 1u)) {
             parity ^= 1u;
             pending &= ~1u;
-            convert_plane<MODE>(S.raw[0], S.W[0], -2, kc, st);
+            convert_plane<MODE>(S.raw[0], S.W[0], plane_read_bits(rmask, -2), kc, st);
         } else {
             timed_out = true;
         }
@@ -186,7 +187,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
-                convert_plane<MODE>(S.raw[s], S.W[(s == 1) ? 1 : 2], (s == 1) ? -1 : 0, kc, st);
+                convert_plane<MODE>(S.raw[s], S.W[(s == 1) ? 1 : 2],
+                                    plane_read_bits(rmask, (s == 1) ? -1 : 0), kc, st);
             } else {
                 timed_out = true;
             }
@@ -345,7 +347,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
-                        convert_plane<MODE>(S.raw[slot], S.W[(k + 4) % 3], k + 2, kc, st);
+                        convert_plane<MODE>(S.raw[slot], S.W[(k + 4) % 3],
+                                            plane_read_bits(rmask, k + 2), kc, st);
                     } else {
                         timed_out = true;
                     }
