@@ -78,7 +78,12 @@ typedef struct gh_params {
                                    it is raised to it, momentum kept                         */
     double p_floor;             /* finite, >= 0; 0 = off (default): where the updated density
                                    is positive and the pressure below p_floor, the total
-                                   energy becomes |m|^2/(2 rho) + p_floor/(gamma - 1)        */
+                                   energy becomes |m|^2/(2 rho) + p_floor/(gamma - 1)
+                                   (at least 4 eps |m|^2/(2 rho), eps of the storage type) */
+    int32_t reconstruction;     /* slopes limited in 0: the primitive variables (default;
+                                   the paper's reading), 1: the characteristic variables
+                                   of each direction (a scheme variant)                    */
+    int32_t reserved;           /* must be 0                                                */
 } gh_params;
 
 /*

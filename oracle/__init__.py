@@ -60,7 +60,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("limiter", ctypes.c_int32),
                 ("predictor_fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
                 ("p_floor", ctypes.c_double), ("flux_layout", ctypes.c_int32),
-                ("riemann", ctypes.c_int32)]
+                ("riemann", ctypes.c_int32), ("reconstruction", ctypes.c_int32)]
 
 
 def _load():
@@ -88,6 +88,7 @@ def _load():
         lib.oracle_roe_flux.argtypes = [ctypes.c_int, pd, pd, d, ctypes.c_int, pd]
         lib.oracle_hlle_flux.argtypes = [ctypes.c_int, pd, pd, d, pd]
         lib.oracle_hllc_flux.argtypes = [ctypes.c_int, pd, pd, d, pd]
+        lib.oracle_char_slopes.argtypes = [ctypes.c_int, pd, pd, pd, d, ctypes.c_int, pd]
         lib.oracle_exact_riemann_star.argtypes = [d, d, d, d, d, d, d, pd]
         lib.oracle_exact_riemann_sample.argtypes = [d, d, d, d, d, d, d, d, pd]
         lib.oracle_count_ops_group.argtypes = [pd, d, d, P(_Params), pd]
@@ -111,9 +112,9 @@ def _ptr(a, ctype=ctypes.c_double):
 
 
 def _params(gamma, limiter, predictor_fallback, rho_floor=0.0, p_floor=0.0, flux_layout=0,
-            riemann=0):
+            riemann=0, reconstruction=0):
     return _Params(float(gamma), int(limiter), int(predictor_fallback), float(rho_floor),
-                   float(p_floor), int(flux_layout), int(riemann))
+                   float(p_floor), int(flux_layout), int(riemann), int(reconstruction))
 
 
 def _f64(a):
@@ -121,7 +122,7 @@ def _f64(a):
 
 
 def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_floor=0.0,
-                p_floor=0.0, flux_layout=0, riemann=0):
+                p_floor=0.0, flux_layout=0, riemann=0, reconstruction=0):
     """One step on a ghost-padded box U_in[5][nz+4][ny+4][nx+4].
 
     Returns (out[5][nz][ny][nx], face_flux (list of 6 arrays: -x, +x, -y, +y,
@@ -135,7 +136,8 @@ def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_fl
     ff = np.empty(per * 5 * (nz * ny + nz * nx + ny * nx))
     st = np.zeros(1, dtype=np.uint32)
     part = np.empty(6)
-    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout, riemann)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout, riemann,
+                reconstruction)
     rc = _load().oracle_advance_box(_ptr(U_in), nx, ny, nz, _ptr(out), _ptr(ff), float(dt),
                                     float(dh), ctypes.byref(p), _ptr(st, ctypes.c_uint32),
                                     _ptr(part))
@@ -150,7 +152,8 @@ def advance_box(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, rho_fl
 
 
 def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nthreads=1,
-                   want_flux=True, rho_floor=0.0, p_floor=0.0, flux_layout=0, riemann=0):
+                   want_flux=True, rho_floor=0.0, p_floor=0.0, flux_layout=0, riemann=0,
+                   reconstruction=0):
     """N independent patch groups U_in[N][5][20][20][20] (dt, dh scalars or [N]).
 
     Returns (out[N][5][16][16][16], face_flux[N][6 or 9][5][16][16] or None,
@@ -164,7 +167,8 @@ def advance_groups(U_in, dt, dh, gamma=1.4, limiter=0, predictor_fallback=0, nth
     ff = np.empty((N, 9 if flux_layout == 1 else 6, 5, 16, 16)) if want_flux else None
     st = np.zeros(N, dtype=np.uint32)
     part = np.empty((N, 6))
-    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout, riemann)
+    p = _params(gamma, limiter, predictor_fallback, rho_floor, p_floor, flux_layout, riemann,
+                reconstruction)
     rc = _load().oracle_advance_groups(_ptr(U_in), _ptr(out), _ptr(ff), _ptr(dt), _ptr(dh), N,
                                        ctypes.byref(p), _ptr(st, ctypes.c_uint32), _ptr(part),
                                        int(nthreads))
@@ -282,6 +286,15 @@ def hlle_flux(d, UL, UR, gamma):
     F = np.empty(5)
     _load().oracle_hlle_flux(int(d), _ptr(UL), _ptr(UR), float(gamma), _ptr(F))
     return F
+
+
+def char_slopes(d, Wl, Wc, Wr, gamma, limiter=0):
+    """Characteristic-limited slope (primitive variables) of Wc along d."""
+    Wl, Wc, Wr = _f64(Wl), _f64(Wc), _f64(Wr)
+    s = np.empty(5)
+    _load().oracle_char_slopes(int(d), _ptr(Wl), _ptr(Wc), _ptr(Wr), float(gamma), int(limiter),
+                               _ptr(s))
+    return s
 
 
 def hllc_flux(d, UL, UR, gamma):

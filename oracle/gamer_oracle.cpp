@@ -88,6 +88,7 @@ struct Scheme {
     R p_floor = R(0.0);    // 0: off
     int flux_layout = 0;   // 0: six box faces, 1: nine planes
     int solver = 0;        // Riemann solver: 0 Roe (with HLLE fallback), 1 HLLC
+    int recon = 0;         // slopes limited in 0: primitive, 1: characteristic variables
 
     // Conserved -> primitive.  p = (gamma-1) (E - 0.5 |m|^2 / rho).
     void prim(const R U[5], R W[5]) const {
@@ -121,6 +122,48 @@ struct Scheme {
         F[1 + d] = F[1 + d] + W[4];
         F[4] = (E + W[4]) * un;
     }
+    // READING R21 (scheme variant): slopes limited in the characteristic
+    // variables of the primitive Euler system along direction d, at the cell's
+    // own state (rho, u_n, u_t1, u_t2, p; c^2 = gamma p / rho):
+    //   left eigenvectors  l1 = (0, -rho/(2c), 0, 0, 1/(2c^2)), l2 = (1, 0, 0, 0, -1/c^2),
+    //                      l3 = e_t1, l4 = e_t2, l5 = (0, rho/(2c), 0, 0, 1/(2c^2));
+    //   right eigenvectors r1 = (1, -c/rho, 0, 0, c^2), r2 = e_rho, r3 = e_t1,
+    //                      r4 = e_t2, r5 = (1, c/rho, 0, 0, c^2).
+    // Each characteristic component is limited from its left and right
+    // differences and the slope is projected back; where c^2 <= 0 the
+    // primitive slopes are used.
+    void char_slopes(int d, const R Wl[5], const R Wc[5], const R Wr[5], R sl[5]) const {
+        const R c2 = gamma * Wc[4] / Wc[0];
+        if (!(c2 > R(0.0))) {
+            for (int q = 0; q < 5; ++q) sl[q] = limit(Wc[q] - Wl[q], Wr[q] - Wc[q]);
+            return;
+        }
+        const int n = 1 + d, t1 = 1 + (d + 1) % 3, t2 = 1 + (d + 2) % 3;
+        const R c = r_sqrt(c2);
+        R dl[5], dr[5];
+        for (int q = 0; q < 5; ++q) {
+            dl[q] = Wc[q] - Wl[q];
+            dr[q] = Wr[q] - Wc[q];
+        }
+        R al[5], ar[5];
+        const R* dW[2] = {dl, dr};
+        R* a[2] = {al, ar};
+        for (int s = 0; s < 2; ++s) {
+            a[s][0] = R(0.5) * (dW[s][4] / c2 - Wc[0] * dW[s][n] / c);
+            a[s][1] = dW[s][0] - dW[s][4] / c2;
+            a[s][2] = dW[s][t1];
+            a[s][3] = dW[s][t2];
+            a[s][4] = R(0.5) * (dW[s][4] / c2 + Wc[0] * dW[s][n] / c);
+        }
+        R da[5];
+        for (int k = 0; k < 5; ++k) da[k] = limit(al[k], ar[k]);
+        sl[0] = da[0] + da[1] + da[4];
+        sl[n] = c / Wc[0] * (da[4] - da[0]);
+        sl[t1] = da[2];
+        sl[t2] = da[3];
+        sl[4] = c2 * (da[0] + da[4]);
+    }
+
     // READING R2: limited slope from the left and right differences.
     R limit(R a, R b) const {
         if (!(a * b > R(0.0))) return R(0.0);
@@ -386,10 +429,15 @@ int advance_box(const Scheme<R>& S, const R* in, int nx, int ny, int nz, R* out,
                     const int di = (d == 0), dj = (d == 1), dk = (d == 2);
                     const R* Wl = &W[pidx(i - di, j - dj, k - dk) * 5];
                     const R* Wr = &W[pidx(i + di, j + dj, k + dk) * 5];
+                    R slope[5];
+                    if (S.recon == 1) {
+                        S.char_slopes(d, Wl, Wc, Wr, slope);
+                    } else {
+                        for (int q = 0; q < 5; ++q) slope[q] = S.limit(Wc[q] - Wl[q], Wr[q] - Wc[q]);
+                    }
                     for (int q = 0; q < 5; ++q) {
-                        R slope = S.limit(Wc[q] - Wl[q], Wr[q] - Wc[q]);
-                        Wf[2 * d][q] = Wc[q] - R(0.5) * slope;
-                        Wf[2 * d + 1][q] = Wc[q] + R(0.5) * slope;
+                        Wf[2 * d][q] = Wc[q] - R(0.5) * slope[q];
+                        Wf[2 * d + 1][q] = Wc[q] + R(0.5) * slope[q];
                     }
                     S.cons(Wf[2 * d], Uf[2 * d]);
                     S.cons(Wf[2 * d + 1], Uf[2 * d + 1]);
@@ -548,6 +596,7 @@ Scheme<R> make_scheme(const oracle_params* p) {
     S.p_floor = R(p->p_floor);
     S.flux_layout = p->flux_layout;
     S.solver = p->riemann;
+    S.recon = p->reconstruction;
     return S;
 }
 
@@ -556,7 +605,8 @@ bool params_ok(const oracle_params* p) {
            (p->predictor_fallback == 0 || p->predictor_fallback == 1) &&
            std::isfinite(p->rho_floor) && p->rho_floor >= 0.0 && std::isfinite(p->p_floor) &&
            p->p_floor >= 0.0 && (p->flux_layout == 0 || p->flux_layout == 1) &&
-           (p->riemann == 0 || p->riemann == 1);
+           (p->riemann == 0 || p->riemann == 1) &&
+           (p->reconstruction == 0 || p->reconstruction == 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -678,6 +728,13 @@ int oracle_roe_flux(int dir, const double UL[5], const double UR[5], double gamm
     oracle_params p = {gamma, 0, 0};
     return make_scheme<double>(&p).roe(dir, UL, UR, entropy_fix != 0, F) ? 1 : 0;
 }
+void oracle_char_slopes(int dir, const double Wl[5], const double Wc[5], const double Wr[5],
+                        double gamma, int limiter, double slope[5]) {
+    oracle_params p = {gamma, limiter, 0};
+    Scheme<double> S = make_scheme<double>(&p);
+    S.char_slopes(dir, Wl, Wc, Wr, slope);
+}
+
 void oracle_hllc_flux(int dir, const double UL[5], const double UR[5], double gamma, double F[5]) {
     oracle_params p = {gamma, 0, 0};
     p.riemann = 1;

@@ -39,6 +39,8 @@ typedef struct {
     int32_t flux_layout;     /* 0: six box faces; 1: nine planes, three per direction
                                 at 0, n/2 and n cells (n even)                       */
     int32_t riemann;         /* 0: Roe with HLLE fallback (the paper's); 1: HLLC     */
+    int32_t reconstruction;  /* slopes limited in 0: primitive variables (the paper's
+                                reading), 1: characteristic variables                */
 } oracle_params;
 
 /* status bits (per box / per group) */
@@ -123,6 +125,10 @@ void oracle_prim_from_cons(const double U[5], double gamma, double W[5]);
 void oracle_cons_from_prim(const double W[5], double gamma, double U[5]);
 void oracle_euler_flux(int dir, const double W[5], double E, double F[5]);
 double oracle_limiter(int id, double a, double b);
+/* Characteristic-limited slope of the primitive state Wc (rho, vx, vy, vz, p)
+ * along dir from its neighbours Wl, Wr (scheme variant). */
+void oracle_char_slopes(int dir, const double Wl[5], const double Wc[5], const double Wr[5],
+                        double gamma, int limiter, double slope[5]);
 /* HLLC flux (scheme variant) in direction dir from conserved L/R states. */
 void oracle_hllc_flux(int dir, const double UL[5], const double UR[5], double gamma, double F[5]);
 /* Roe flux in direction dir from conserved L/R states; returns 1 when the HLLE

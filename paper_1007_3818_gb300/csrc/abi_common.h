@@ -27,7 +27,8 @@ inline int check_params(const gh_params* p) {
     if (!std::isfinite(p->gamma) || !(p->gamma > 1.0)) return GAMER_E_PARAM;
     if (p->limiter < 0 || p->limiter > 2) return GAMER_E_PARAM;
     if (p->predictor_fallback != 0 && p->predictor_fallback != 1) return GAMER_E_PARAM;
-    if ((p->flux_layout != 0 && p->flux_layout != 1) || (p->riemann != 0 && p->riemann != 1))
+    if ((p->flux_layout != 0 && p->flux_layout != 1) || (p->riemann != 0 && p->riemann != 1) ||
+        (p->reconstruction != 0 && p->reconstruction != 1) || p->reserved != 0)
         return GAMER_E_PARAM;
     if (!std::isfinite(p->rho_floor) || p->rho_floor < 0.0 || !std::isfinite(p->p_floor) ||
         p->p_floor < 0.0)

@@ -453,7 +453,8 @@ __device__ __forceinline__ void hllc_rot(const T L[5], const T R[5], const KCons
 }
 
 // Riemann solve by variant: 0 Roe inline, 1 Roe through one out-of-line
-// copy, 2 HLLC inline.
+// copy, 2 HLLC inline.  (The kernel's RSV template argument carries this in
+// bits 0-1 and the reconstruction, 0 primitive / 1 characteristic, in bit 2.)
 template <int RSV> struct RoeTag {};
 template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_pick(RoeTag<0>, const T L[5], const T R[5],
@@ -520,12 +521,63 @@ __device__ __forceinline__ void flux_diff(const T wm[5], T Em, const T wp[5], T 
     for (int q = 0; q < 5; ++q) acc[q] = acc[q] + (fm[q] - fp[q]);
 }
 
+// Limited slopes of the cell state wc along direction d from its neighbours
+// lo, hi (plane arrays, stride kPlane).  REC 0: per primitive component;
+// REC 1: in the characteristic variables of the primitive Euler system along
+// d (left eigenvectors l1 = (0, -rho/(2c), 0, 0, 1/(2c^2)), l2 = (1, 0, 0, 0,
+// -1/c^2), l3 = e_t1, l4 = e_t2, l5 = (0, rho/(2c), 0, 0, 1/(2c^2)); right
+// eigenvectors r1 = (1, -c/rho, 0, 0, c^2), r2 = e_rho, r3 = e_t1, r4 = e_t2,
+// r5 = (1, c/rho, 0, 0, c^2)), primitive where c^2 <= 0.
+template <int REC> struct RecTag {};
+template <int LIM, class T, class P>
+__device__ __forceinline__ void slopes(RecTag<0>, int, const T* __restrict__ lo, const T wc[5],
+                                       const T* __restrict__ hi, const KConst<T, P>& kc,
+                                       T s[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s[q] = limit<LIM>(wc[q] - lo[q * kPlane], hi[q * kPlane] - wc[q], kc);
+}
+template <int LIM, class T, class P>
+__device__ __forceinline__ void slopes(RecTag<1>, int d, const T* __restrict__ lo, const T wc[5],
+                                       const T* __restrict__ hi, const KConst<T, P>& kc,
+                                       T s[5]) {
+    T dl[5], dr[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        dl[q] = wc[q] - lo[q * kPlane];
+        dr[q] = hi[q * kPlane] - wc[q];
+    }
+    const T ir = rcp_(wc[0]);
+    const T c2 = kc.gamma * wc[4] * ir;
+    if (!(c2 > T(0))) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s[q] = limit<LIM>(dl[q], dr[q], kc);
+        return;
+    }
+    const int n = 1 + d, t1 = 1 + (d + 1) % 3, t2 = 1 + (d + 2) % 3;
+    const T c = sqrt_(c2), ic2 = rcp_(c2);
+    const T rc = wc[0] * rcp_(c);  // rho / c
+    T da[5];
+    {
+        const T pl = dl[4] * ic2, pr = dr[4] * ic2, ul = rc * dl[n], ur = rc * dr[n];
+        da[0] = limit<LIM>(T(0.5) * (pl - ul), T(0.5) * (pr - ur), kc);
+        da[1] = limit<LIM>(dl[0] - pl, dr[0] - pr, kc);
+        da[2] = limit<LIM>(dl[t1], dr[t1], kc);
+        da[3] = limit<LIM>(dl[t2], dr[t2], kc);
+        da[4] = limit<LIM>(T(0.5) * (pl + ul), T(0.5) * (pr + ur), kc);
+    }
+    s[0] = da[0] + da[1] + da[4];
+    s[n] = c * ir * (da[4] - da[0]);
+    s[t1] = da[2];
+    s[t2] = da[3];
+    s[4] = c2 * (da[0] + da[4]);
+}
+
 // Hancock half-step for the cell at plane index c (20x20 plane layout) of
 // plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1.  Branch-free part:
 // fs[f] receives the evolved conserved face states x-, x+, y-, y+, z-, z+,
 // du the common half-step increment; returns whether all six are admissible
 // (rho > 0, p > 0).
-template <int MODE, int LIM, class T, class P>
+template <int MODE, int LIM, int REC = 0, class T, class P>
 __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* __restrict__ W0,
                                              const T* __restrict__ Wp, int c, T half_lam,
                                              T igm1, const KConst<T, P>& kc, T fs[6][5],
@@ -538,12 +590,12 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
     for (int d = 0; d < 3; ++d) {
         const T* lo = (d == 2) ? Wm + c : W0 + c - (d == 0 ? 1 : 20);
         const T* hi = (d == 2) ? Wp + c : W0 + c + (d == 0 ? 1 : 20);
-        T wm[5], wp[5];
+        T wm[5], wp[5], sl[5];
+        slopes<LIM>(RecTag<REC>(), d, lo, wc, hi, kc, sl);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            const T s = limit<LIM>(wc[q] - lo[q * kPlane], hi[q * kPlane] - wc[q], kc);
-            wm[q] = wc[q] - T(0.5) * s;
-            wp[q] = wc[q] + T(0.5) * s;
+            wm[q] = wc[q] - T(0.5) * sl[q];
+            wp[q] = wc[q] + T(0.5) * sl[q];
         }
         cons<T>(wm, fs[2 * d], igm1);
         cons<T>(wp, fs[2 * d + 1], igm1);
@@ -574,13 +626,13 @@ __device__ __forceinline__ void predict_fallback(const T uc[5], const T du[5],
         for (int q = 0; q < 5; ++q) fs[f][q] = (kc.pfb == 0) ? uc[q] : fs[f][q] - du[q];
 }
 
-template <int MODE, int LIM = -1, class T, class P>
+template <int MODE, int LIM = -1, int REC = 0, class T, class P>
 __device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
                                         const T* __restrict__ Wp, const T uc[5], int c,
                                         T half_lam, T igm1, const KConst<T, P>& kc,
                                         T fs[6][5], uint32_t& st) {
     T du[5];
-    if (!predict_core<MODE, LIM>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du)) {
+    if (!predict_core<MODE, LIM, REC>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du)) {
         st |= GAMER_ST_PREDICTOR_FALLBACK;
         predict_fallback(uc, du, kc, fs);
     }
@@ -853,6 +905,8 @@ template <> struct SumAcc<float> {
 // SRC 0: `in` holds N ghost-padded 20^3 tiles, loaded plane by plane with the
 // TMA engine; SRC 1: `in` is the uniform level `geo` (N = gx*gy*gz groups) and
 // each plane is gathered from the group and its neighbours (fused ghost fill).
+// RSV: bits 0-1 the Riemann solver (0 Roe inline, 1 Roe out of line, 2 HLLC),
+// bit 2 characteristic (1) or primitive (0) slope limiting.
 // RING: input planes in flight (2: the copy of plane k+2 goes out after phase A
 // of plane k; 3: plane k+3 does, one full iteration ahead of its use).
 template <int MODE, int MINB, int RSV = 0, int SRC = 0, int RING = 2>
@@ -1043,7 +1097,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
                     T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs, st);
+                    predict<MODE, -1, (RSV >> 2)>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs,
+                                                  st);
                     if (inner) {
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
@@ -1063,7 +1118,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc_b];
                     T fs[6][5];
-                    predict<MODE>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs, st);
+                    predict<MODE, -1, (RSV >> 2)>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs,
+                                                  st);
                     if (inner) {
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
@@ -1093,7 +1149,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T L[5] = {zp0[0], zp0[3], zp0[1], zp0[2], zp0[4]};
                         T R[5] = {zm0[0], zm0[3], zm0[1], zm0[2], zm0[4]};
                         T F[5];
-                        roe_solve<MODE, RSV>(L, R, kc, F, st);
+                        roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
                         fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
                         const int pz = flux_plane(2, k, kc.flux9);
                         if (gff && pz >= 0) {
@@ -1106,7 +1162,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         T L[5] = {zp1[0], zp1[3], zp1[1], zp1[2], zp1[4]};
                         T R[5] = {zm1[0], zm1[3], zm1[1], zm1[2], zm1[4]};
                         T F[5];
-                        roe_solve<MODE, RSV>(L, R, kc, F, st);
+                        roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
                         fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
                         const int pz = flux_plane(2, k, kc.flux9);
                         if (gff && pz >= 0) {
@@ -1158,7 +1214,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         R[2] = RA[c2 * kFaceStride + hi];
                         R[3] = RA[c3 * kFaceStride + hi];
                         R[4] = RA[4 * kFaceStride + hi];
-                        roe_solve<MODE, RSV>(L, R, kc, F, st);
+                        roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
                         S.fxy[wr] = F[0];
                         S.fxy[c1 * kFluxStride + wr] = F[1];
                         S.fxy[c2 * kFluxStride + wr] = F[2];

@@ -68,11 +68,14 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     // Riemann solver out of line; 2 (tiles only) -- two interleaved problems
     // per thread (pair kernel, 2 CTAs/SM in FP32, 1 in FP64), van Leer limiter
     // compiled in plus a runtime-limiter build for the others.  The HLLC
-    // solver (p->riemann = 1) comes in the default shape only (3 CTAs/SM in
-    // FP32 modes, 1 in FP64) and overrides the variant and CTA settings.
+    // solver (p->riemann = 1) and characteristic limiting (p->reconstruction
+    // = 1) come in the default shape only (3 CTAs/SM in FP32 modes, 1 in
+    // FP64) and override the variant and CTA settings.
     const bool hllc = p->riemann == 1;
+    const bool chr = p->reconstruction == 1;
+    const bool special = hllc || chr;  // builds in the default shape only
     if constexpr (SRC == 0) {
-      if (var == 2 && !hllc) {
+      if (var == 2 && !special) {
         constexpr int MB = (MODE == GAMER_MODE_F64) ? 1 : 2;
         auto kern = (p->limiter == 0) ? hydro_pair_kernel<MODE, MB, 0>
                                       : hydro_pair_kernel<MODE, MB, -1>;
@@ -112,11 +115,17 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
             if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
         }
     }
-    if (hllc) {
+    if (special) {
+        // Riemann solver in bits 0-1, characteristic limiting in bit 2
+        const int rsv = (hllc ? 2 : 0) | (chr ? 4 : 0);
         if constexpr (MODE == GAMER_MODE_F64) {
-            kern = hydro_step_kernel<MODE, 1, 2, SRC, 3>;
+            kern = rsv == 2   ? hydro_step_kernel<MODE, 1, 2, SRC, 3>
+                   : rsv == 4 ? hydro_step_kernel<MODE, 1, 4, SRC, 3>
+                              : hydro_step_kernel<MODE, 1, 6, SRC, 3>;
         } else {
-            kern = hydro_step_kernel<MODE, 3, 2, SRC, 2>;
+            kern = rsv == 2   ? hydro_step_kernel<MODE, 3, 2, SRC, 2>
+                   : rsv == 4 ? hydro_step_kernel<MODE, 3, 4, SRC, 2>
+                              : hydro_step_kernel<MODE, 3, 6, SRC, 2>;
             smem = int(sizeof(Smem<T, 2>)) + extra;
         }
     }
@@ -128,7 +137,7 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
             cudaSuccess ||
         per_sm < 1)
         return GAMER_E_CUDA;
-    if (want > 0 && want < per_sm && !hllc) per_sm = want;
+    if (want > 0 && want < per_sm && !special) per_sm = want;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
     kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh, status,
                                                             partials, N, kc, geo);

@@ -34,16 +34,18 @@ class gh_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("limiter", ctypes.c_int32), ("predictor_fallback", ctypes.c_int32),
                 ("flux_layout", ctypes.c_int32), ("riemann", ctypes.c_int32),
-                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
+                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
+                ("reconstruction", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 FLUX_PLANES = {0: 6, 1: 9}  # face-flux planes per group by gh_params.flux_layout
 
 
 def make_params(gamma, cfl=0.5, limiter=0, predictor_fallback=0, rho_floor=0.0, p_floor=0.0,
-                flux_layout=0, riemann=0):
+                flux_layout=0, riemann=0, reconstruction=0):
     return gh_params(float(gamma), float(cfl), int(limiter), int(predictor_fallback),
-                     int(flux_layout), int(riemann), float(rho_floor), float(p_floor))
+                     int(flux_layout), int(riemann), float(rho_floor), float(p_floor),
+                     int(reconstruction), 0)
 
 
 def lib():

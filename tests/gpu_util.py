@@ -24,7 +24,7 @@ def host_input(tiles, mode):
 
 
 def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, with_flux=True,
-                rho_floor=0.0, p_floor=0.0, riemann=0):
+                rho_floor=0.0, p_floor=0.0, riemann=0, reconstruction=0):
     """One step on the GPU; returns numpy (out, face_flux, status, partials)."""
     import torch
     from paper_1007_3818_gb300 import native
@@ -38,7 +38,8 @@ def gpu_advance(tiles, dt, dh, gamma, mode, limiter=0, predictor_fallback=0, wit
     d_st = torch.full((N,), -1, device="cuda", dtype=torch.int32)
     d_part = torch.full((N, 6), float("nan"), device="cuda", dtype=torch.float64)
     params = native.make_params(gamma, limiter=limiter, predictor_fallback=predictor_fallback,
-                                rho_floor=rho_floor, p_floor=p_floor, riemann=riemann)
+                                rho_floor=rho_floor, p_floor=p_floor, riemann=riemann,
+                                reconstruction=reconstruction)
     native.hydro_advance(mode, d_in, d_out, d_ff, d_dt, d_dh, d_st, d_part, params)
     torch.cuda.synchronize()
     ff = d_ff.double().cpu().numpy() if with_flux else None
@@ -81,15 +82,16 @@ def flux_rel_l1(a, b):
 
 
 def compare_step(tiles, dt, dh, gamma, mode, tol, limiter=0, predictor_fallback=0,
-                 check_status=True, riemann=0):
+                 check_status=True, riemann=0, reconstruction=0):
     """GPU vs oracle for one step of the given tiles; returns the error dict."""
     import oracle
     host = host_input(tiles, mode)
     out, ff, st, part = gpu_advance(host, dt, dh, gamma, mode, limiter, predictor_fallback,
-                                    riemann=riemann)
+                                    riemann=riemann, reconstruction=reconstruction)
     r_out, r_ff, r_st, r_part = oracle.advance_groups(host, dt, dh, gamma=gamma, limiter=limiter,
                                                       predictor_fallback=predictor_fallback,
-                                                      riemann=riemann)
+                                                      riemann=riemann,
+                                                      reconstruction=reconstruction)
     err = {
         "out": rel_l1_fields(out, r_out),
         "flux": flux_rel_l1(ff, r_ff),

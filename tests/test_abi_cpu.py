@@ -78,6 +78,10 @@ def test_advance_rejects_bad_arguments(lib, name):
     assert _adv(lib, name, params=native.make_params(1.4, limiter=3)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, predictor_fallback=2)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, riemann=2)) == -2
+    assert _adv(lib, name, params=native.make_params(1.4, reconstruction=2)) == -2
+    bad = native.make_params(1.4)
+    bad.reserved = 1
+    assert _adv(lib, name, params=bad) == -2
     assert _adv(lib, name, params=native.make_params(1.4, flux_layout=2)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, rho_floor=-1e-3)) == -2
     assert _adv(lib, name, params=native.make_params(1.4, p_floor=float("nan"))) == -2

@@ -378,6 +378,42 @@ def test_hllc_fused_level_equals_fill_then_step(mode):
 
 
 # --------------------------------------------------------------------------
+# Characteristic-variable limiting (gh_params.reconstruction = 1)
+@pytest.mark.parametrize("riemann", [0, 1], ids=["roe", "hllc"])
+@pytest.mark.parametrize("mode,tol", MODES)
+def test_characteristic_limiting_matches_oracle(mode, tol, riemann):
+    g = 5 / 3
+    compare_step(wl.random_smooth_groups(5, seed=43, gamma=g), 2e-3, 1 / 256, g, mode, tol,
+                 riemann=riemann, reconstruction=1)
+    tiles, level, dh_level = wl.amr_batch(counts=(2, 2, 2), seed=13, base_n=64)
+    compare_step(tiles, 0.3 * dh_level[level] / 4.0, dh_level[level], g, mode, tol,
+                 riemann=riemann, reconstruction=1)
+    for lim in (1, 2):
+        compare_step(wl.random_smooth_groups(2, seed=6, gamma=g), 2e-3, 1 / 256, g, mode, tol,
+                     limiter=lim, riemann=riemann, reconstruction=1)
+
+
+def test_characteristic_limiting_fused_level():
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    gx, gy, gz = 2, 2, 3
+    G = gx * gy * gz
+    lv = np.concatenate([wl.level_to_groups(wl.fourier_level(n=16, seed=90 + i, gamma=g))
+                         for i in range(G)])
+    d_lv = torch.from_numpy(lv).to("cuda", torch.float64)
+    dt = torch.full((G,), 2e-3, device="cuda", dtype=torch.float64)
+    dh = torch.full((G,), 1 / 64, device="cuda", dtype=torch.float64)
+    out = torch.empty_like(d_lv)
+    native.hydro_advance_level(F64, d_lv, out, None, gx, gy, gz, 1, dt, dh, None, None,
+                               native.make_params(g, reconstruction=1))
+    torch.cuda.synchronize()
+    r_out, _, _, _ = oracle.advance_groups(oracle.fill_ghosts_uniform(lv, gx, gy, gz, 1), 2e-3,
+                                           1 / 64, gamma=g, reconstruction=1)
+    assert rel_l1_fields(out.cpu().numpy(), r_out) <= TOL_F64
+
+
+# --------------------------------------------------------------------------
 # Density and pressure floors on the updated state
 @pytest.mark.parametrize("mode", [F32, MIXED, F64], ids=["f32", "mixed", "f64"])
 def test_floors_match_oracle(mode):
