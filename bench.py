@@ -97,7 +97,8 @@ def parse():
     ap.add_argument("--workload", choices=["uniform256", "streamed1024"], default="uniform256",
                     help="uniform256: device-resident 256^3 level (default); streamed1024: "
                          "1024^3 level in pinned host memory streamed through the GPU")
-    ap.add_argument("--batch", type=int, default=4096, help="streamed batch size (groups)")
+    ap.add_argument("--batch", type=int, default=32768,
+                    help="streamed slab size in groups (a multiple of a 4096-group layer)")
     return ap.parse_args()
 
 
@@ -244,9 +245,9 @@ def reference_arm(args):
 
 # --------------------------------------------------------------------------
 def streamed_main(args):
-    """1024^3 level (262,144 groups) in pinned host memory; every step the host
-    threads prepare ghost zones batch by batch while the GPU copies in, steps
-    and copies back the previous batches on three streams."""
+    """1024^3 level (262,144 groups) in pinned host memory; every step streams
+    z-slabs of the interiors (with a halo layer each side) to the device, where
+    the ghost zones are gathered, and the results back, on three streams."""
     import numpy as np
     import torch
     from paper_1007_3818_gb300 import native
@@ -281,8 +282,8 @@ def streamed_main(args):
         cur = 1 - cur
     el = time.perf_counter() - t0
     clk = clocks.stop()
+    h2d, d2h = pl.last_bytes()
     pl.close()
-    esz = 8 if T == torch.float64 else 4
     cells = G * GROUP_CELLS
     v = cells * args.steps / el
     print(json.dumps({
@@ -290,11 +291,12 @@ def streamed_main(args):
         "warmup": 1, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.mode, "data": "synthetic",
         "config": {"workload": "streamed 1024^3 level: 262,144 patch groups in pinned host "
-                               "memory, host ghost fill overlapped with H2D / step / D2H on 3 "
-                               "streams, lognormal density contrast 1e4, gamma 5/3",
-                   "batch_groups": args.batch, "host_threads": os.cpu_count()},
-        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": G * (40000 * esz + 16),
-                "d2h_bytes_per_step": G * (20480 * esz + 52)},
+                               "memory, z-slabs of the interiors with a halo layer each side, "
+                               "ghost gather on the device, H2D / step / D2H on 3 streams, "
+                               "lognormal density contrast 1e4, gamma 5/3",
+                   "slab_groups": args.batch},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "clocks": clk, "status_or": int(np.bitwise_or.reduce(st.numpy())),
     }), flush=True)
     return 0
@@ -425,33 +427,49 @@ def main():
     for g in graphs:
         g.close()
 
-    # end to end through the host-buffer pipeline (same groups, one step/call)
+    # end to end: the same level held in pinned HOST memory, one public call per
+    # step (gamer_pipeline_level_step_host: z-slabs of the level's interiors
+    # with a halo layer each side go to the device, the ghost zones are
+    # gathered there, results and partials come back); the next dt is the
+    # FP64 max over the returned partials, on the host
     e2e = None
     if not args.no_e2e:
-        h_in = tiles.cpu().pin_memory()
-        h_out = torch.empty((G, 5, 16, 16, 16), dtype=T).pin_memory()
-        h_ff = torch.empty((G, 6, 5, 16, 16), dtype=T).pin_memory()
-        h_dt = dt_g.cpu().pin_memory()
-        h_dh = dh_g.cpu().pin_memory()
+        h_lv = [torch.from_numpy(level_h).to(T).pin_memory(),
+                torch.empty((G, 5, 16, 16, 16), dtype=T).pin_memory()]
         h_st = torch.empty(G, dtype=torch.int32).pin_memory()
         h_part = torch.empty((G, 6), dtype=torch.float64).pin_memory()
-        tp = tune.tune_pipeline(mode, h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
-        pipe = native.Pipeline(mode, tp["batch"], with_flux=True)
-        for _ in range(2):
-            pipe.advance_host(h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
+        timing = {}
+        for batch in (256, 512, 1024, 2048):             # slabs of 1, 2, 4, 8 layers
+            pl = native.Pipeline(mode, batch, with_flux=False)
+            pl.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 0.0, dh, h_st, h_part, params)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                pl.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 1e-4, dh, h_st, h_part,
+                                   params)
+            timing[batch] = time.perf_counter() - t0
+            pl.close()
+        batch = min(timing, key=timing.get)
+        pipe = native.Pipeline(mode, batch, with_flux=False)
+        pipe.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 0.0, dh, h_st, h_part, params)
+        cur = 0
         n_e2e = max(3, min(args.steps, 50))
         dist.barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            pipe.advance_host(h_in, h_out, h_ff, h_dt, h_dh, h_st, h_part, params)
+            dt_e = CFL * dh / float(h_part[:, 0].max())
+            pipe.level_step_host(h_lv[cur], h_lv[1 - cur], gx, gy, gz, 0, dt_e, dh, h_st,
+                                 h_part, params)
+            cur = 1 - cur
         el_e2e = dist.max_over_ranks(time.perf_counter() - t0, device=dev)
+        h2d, d2h = pipe.last_bytes()
         pipe.close()
-        h2d = h_in.numel() * esz + 16 * G
-        d2h = (h_out.numel() + h_ff.numel()) * esz + 4 * G + 48 * G
         e2e = {"value": world * cells_per_step * n_e2e / el_e2e, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": n_e2e, "api": "gamer_pipeline_advance_host (pinned host buffers, "
-                                      "3 streams, batches of %d groups)" % tp["batch"]}
+               "steps": n_e2e, "slab_groups": batch,
+               "api": "gamer_pipeline_level_step_host (pinned host level streamed in z-slabs "
+                      "of %d layers through a device copy of the level, each layer once; "
+                      "ghost gather on the device; 3 streams; state, status and partials "
+                      "back)" % (batch // (gx * gy))}
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6702.2)

@@ -160,6 +160,38 @@ int gamer_hydro_advance_level_f64(const double* level, double* out, double* face
                                   double* partials, const gh_params* p, void* stream);
 
 /*
+ * gamer_hydro_advance_level_window_{f32,mixed,f64}: as
+ * gamer_hydro_advance_level_* for the z-layers z0 .. z0+nz-1 of a gx*gy*gz
+ * level of which the device holds only a window: zn consecutive layers
+ * (layer = gx*gy groups, group order as in the level), the first being level
+ * layer zb, the following ones zb+1, ... modulo gz (periodic wrap).  For
+ * streaming a level through device memory in slabs (paper Sec. 3: out-of-core
+ * computation); every layer the step reads (z0-1 .. z0+nz, wrapped for bc 0,
+ * clamped for bc 1) must be in the window.
+ *   window    [zn][gy][gx][5][16][16][16] device memory, 16-byte aligned.
+ *   out, face_flux, dt, dh, status, partials: as gamer_hydro_advance_* with
+ *             N = gx*gy*nz (group g is level group g + z0*gx*gy).
+ * Returns GAMER_E_PARAM for extents as gamer_hydro_advance_level_*, for
+ * z0 < 0, nz < 0, z0 + nz > gz, zb outside [0, gz), zn outside [0, gz], or a
+ * needed layer missing from the window; nz = 0 is a no-op.
+ */
+int gamer_hydro_advance_level_window_f32(const float* window, float* out, float* face_flux,
+                                         int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                         int32_t zb, int32_t zn, int32_t z0, int32_t nz,
+                                         const double* dt, const double* dh, uint32_t* status,
+                                         double* partials, const gh_params* p, void* stream);
+int gamer_hydro_advance_level_window_mixed(const float* window, float* out, float* face_flux,
+                                           int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                           int32_t zb, int32_t zn, int32_t z0, int32_t nz,
+                                           const double* dt, const double* dh, uint32_t* status,
+                                           double* partials, const gh_params* p, void* stream);
+int gamer_hydro_advance_level_window_f64(const double* window, double* out, double* face_flux,
+                                         int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                         int32_t zb, int32_t zn, int32_t z0, int32_t nz,
+                                         const double* dt, const double* dh, uint32_t* status,
+                                         double* partials, const gh_params* p, void* stream);
+
+/*
  * gamer_fill_ghosts_uniform_{f32,f64}: ghost-zone preparation for a uniform
  * level (paper Sec. 2: the ghost-zone data each patch needs before the solver
  * runs).  level[G][5][16][16][16] holds the interiors of G = gx*gy*gz groups,
@@ -271,22 +303,43 @@ int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds);
 
 /*
  * gamer_pipeline_level_step_host: one step of a uniform level that lives in
- * HOST memory (the paper's arrangement: the CPU prepares ghost zones while the
- * GPU solves, Sec. 2).  For each batch of the pipeline's size, host threads
- * (nthreads, <= 0: all) build the ghost-padded tiles from level_in_host into a
- * pinned staging buffer while the GPU copies, advances and copies back the
- * batches queued before it; results go straight into level_out_host.
+ * HOST memory, streamed through the device in z-slabs (paper Sec. 3: a
+ * problem larger than device memory processed piece by piece, transfers
+ * overlapped with computation).  A slab is L layers of gx*gy groups, L*gx*gy
+ * about the pipeline's batch size (at least one layer).  For each slab the 16^3
+ * interiors of its layers and of the layer below and above (periodic wrap or,
+ * for bc 1, the level's end layers) go to the device in at most two copies;
+ * the slab is advanced by gamer_hydro_advance_level_window_* with the ghost
+ * zones gathered on the device; its results come back into level_out_host.
+ * Three slabs are in flight on the pipeline's three streams.  The host does
+ * no ghost preparation: nthreads is ignored.
  * level_in_host, level_out_host [G][5][16]^3 (G = gx*gy*gz, element type by
- * mode, distinct, ideally pinned); bc 0 periodic, 1 zero-gradient; one dt, dh
- * for the level; status_host [G] and partials_host [G][6] may be NULL.  The
- * first call allocates three pinned staging buffers of the batch size (held
- * until gamer_pipeline_destroy); later calls allocate nothing.  Bounded waits
- * as for gamer_pipeline_advance_host; no face fluxes.
+ * mode, distinct, pinned for overlap); bc 0 periodic, 1 zero-gradient; one dt,
+ * dh for the level; status_host [G] and partials_host [G][6] may be NULL.
+ * The first call (and a call on a level whose slabs need more room) allocates
+ * the device window buffers (held until gamer_pipeline_destroy).  Bounded
+ * waits as for gamer_pipeline_advance_host; no face fluxes.
+ *
+ * When the level's input and output fit in 80 % of the free device memory
+ * (or level mode 1 is set), the pipeline keeps a device copy of the whole
+ * level instead (allocated once, held until destroy or level mode 2): each
+ * slab of layers is copied in once, its kernel waits for its own copy and
+ * the next slab's (the layer above) -- the periodic wrap layer goes first --
+ * and its results go back while the next slabs are copied and advanced, so
+ * every layer crosses the link once per step.
+ *
+ * gamer_pipeline_last_bytes: host->device and device->host bytes the last
+ * advance_host or level_step_host call on this pipeline copied.
+ *
+ * gamer_pipeline_set_level_mode: 0 automatic (default), 1 always the device
+ * copy of the level, 2 always slab windows with halo layers (frees the copy).
  */
 int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* level_in_host,
                                    void* level_out_host, int32_t gx, int32_t gy, int32_t gz,
                                    int32_t bc, double dt, double dh, uint32_t* status_host,
                                    double* partials_host, const gh_params* p, int32_t nthreads);
+int gamer_pipeline_last_bytes(const gamer_pipeline* pl, int64_t* h2d, int64_t* d2h);
+int gamer_pipeline_set_level_mode(gamer_pipeline* pl, int32_t mode);
 
 /*
  * gamer_fill_ghosts_uniform_host_{f32,f64}: gamer_fill_ghosts_uniform_* on

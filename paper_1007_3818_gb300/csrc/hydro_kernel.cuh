@@ -716,9 +716,13 @@ __device__ __forceinline__ void issue_plane(SM& S, const T* gin, int kp) {
 
 // Uniform level read directly by the kernel (fused ghost gather): gx*gy*gz
 // groups of [5][16][16][16], group id (z*gy + y)*gx + x, periodic (bc 0) or
-// zero-gradient (bc 1) boundaries.
+// zero-gradient (bc 1) boundaries.  The device buffer may hold a window of the
+// level: its layer l (of gx*gy groups) is the level's z-layer (zb + l) mod gz;
+// the kernel's group g is the level's group g + z0*gx*gy.  The whole level is
+// zb = z0 = 0.
 struct LevelGeom {
     int gx, gy, gz, bc;
+    int zb, z0;
 };
 
 // Level coordinate X, at most two cells outside [0, n), mapped into the level:
@@ -817,7 +821,9 @@ __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
     const int slot = (kp + 2) % RING;
     T* plane = S.raw[slot] + raw_offset<1, T>();
     const int Z = wrap_near(bz * 16 + kp, 16 * L.gz, L.bc);
-    const T* lz = level + int64_t(Z >> 4) * (L.gy * L.gx) * 20480 + (Z & 15) * 256;
+    int zl = (Z >> 4) - L.zb;  // window layer of the group layer holding Z
+    zl += (zl < 0) ? L.gz : 0;
+    const T* lz = level + int64_t(zl) * (L.gy * L.gx) * 20480 + (Z & 15) * 256;
     const int dk = ghost_depth(kp + 2);
     if (ghost_depth(w.j) + dk <= 2) {
         const T* src = lz + int64_t(P.chunk) * 16 + w.q * G::E16;
@@ -869,7 +875,7 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
                                            GatherPlan* plan_)
         : level(in), L(geo), plan(plan_ + threadIdx.x) {
         const int bx = int(g % geo.gx), by = int((g / geo.gx) % geo.gy);
-        bz = int(g / (int64_t(geo.gx) * geo.gy));
+        bz = geo.z0 + int(g / (int64_t(geo.gx) * geo.gy));
         *plan = make_plan<T>(geo, bx, by);  // read back by this thread only
     }
     template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {

@@ -19,7 +19,7 @@ template <int MODE, int SRC>
 int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                  typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
                  uint32_t* status, double* partials, int64_t N, const gh_params* p,
-                 LevelGeom geo, void* stream) {
+                 LevelGeom geo, void* stream, int64_t win_layers = 0) {
     using T = typename Prec<MODE>::T;
     using P = typename Prec<MODE>::P;
     if (N < 0) return GAMER_E_PARAM;
@@ -30,7 +30,10 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     if (!aligned(in, 16) || !aligned(out, sizeof(T)) || !aligned(face_flux, sizeof(T)) ||
         !aligned(dt, 8) || !aligned(dh, 8) || !aligned(status, 4) || !aligned(partials, 8))
         return GAMER_E_ALIGN;
-    const size_t nin = size_t(N) * (SRC == 0 ? 40000 : 20480) * sizeof(T);
+    // input: N tiles, or the window of win_layers z-layers of the level
+    const size_t nin = (SRC == 0 ? size_t(N) * 40000
+                                 : size_t(win_layers) * size_t(geo.gx) * size_t(geo.gy) * 20480) *
+                       sizeof(T);
     const size_t nout = size_t(N) * 20480 * sizeof(T);
     const size_t nff =
         face_flux ? size_t(N) * (p->flux_layout ? 9 : 6) * 1280 * sizeof(T) : 0;
@@ -149,7 +152,7 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                   typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
                   uint32_t* status, double* partials, int64_t N, const gh_params* p,
                   void* stream) {
-    const LevelGeom geo = {1, 1, 1, 0};
+    const LevelGeom geo = {1, 1, 1, 0, 0, 0};
     return hydro_launch<MODE, 0>(in, out, face_flux, dt, dh, status, partials, N, p, geo,
                                  stream);
 }
@@ -166,9 +169,40 @@ int hydro_advance_level(const typename Prec<MODE>::T* level, typename Prec<MODE>
     // the gather's per-group plan holds level offsets within a z-layer of
     // groups in units of 16 cells as 32-bit integers
     if (int64_t(gx) * gy * 1280 + 2048 > INT32_MAX) return GAMER_E_PARAM;
-    const LevelGeom geo = {gx, gy, gz, bc};
+    const LevelGeom geo = {gx, gy, gz, bc, 0, 0};
     return hydro_launch<MODE, 1>(level, out, face_flux, dt, dh, status, partials,
-                                 int64_t(gx) * gy * gz, p, geo, stream);
+                                 int64_t(gx) * gy * gz, p, geo, stream, gz);
+}
+
+// Layers z0 .. z0+nz-1 of the level from a window of zn layers starting at
+// level layer zb (periodic wrap); every layer the stencil reads must be in it.
+template <int MODE>
+int hydro_advance_level_window(const typename Prec<MODE>::T* window, typename Prec<MODE>::T* out,
+                               typename Prec<MODE>::T* face_flux, int32_t gx, int32_t gy,
+                               int32_t gz, int32_t bc, int32_t zb, int32_t zn, int32_t z0,
+                               int32_t nz, const double* dt, const double* dh, uint32_t* status,
+                               double* partials, const gh_params* p, void* stream) {
+    if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1)) return GAMER_E_PARAM;
+    if (int64_t(gx) * 16 > (1 << 30) || int64_t(gy) * 16 > (1 << 30) ||
+        int64_t(gz) * 16 > (1 << 30))
+        return GAMER_E_PARAM;
+    if (int64_t(gx) * gy * 1280 + 2048 > INT32_MAX) return GAMER_E_PARAM;
+    if (nz < 0 || z0 < 0 || int64_t(z0) + nz > gz || zb < 0 || zb >= (gz > 0 ? gz : 1) ||
+        zn < 0 || zn > gz)
+        return GAMER_E_PARAM;
+    if (nz == 0 || gx == 0 || gy == 0) return GAMER_OK;
+    // every layer read (z0 - 1 .. z0 + nz, wrapped or clamped) lies in the window
+    for (int64_t z = int64_t(z0) - 1; z <= int64_t(z0) + nz; ++z) {
+        int64_t zz = z;
+        if (zz < 0 || zz >= gz) {
+            if (bc == 1) continue;  // zero-gradient: the clamped layer is an end layer, read anyway
+            zz = (zz + gz) % gz;
+        }
+        if ((zz - zb + gz) % gz >= zn) return GAMER_E_PARAM;
+    }
+    const LevelGeom geo = {gx, gy, gz, bc, zb, z0};
+    return hydro_launch<MODE, 1>(window, out, face_flux, dt, dh, status, partials,
+                                 int64_t(gx) * gy * nz, p, geo, stream, zn);
 }
 
 }  // namespace gamer

@@ -18,3 +18,11 @@ extern "C" int gamer_hydro_advance_level_mixed(const float* level, float* out, f
     return gamer::hydro_advance_level<GAMER_MODE_MIXED>(level, out, face_flux, gx, gy, gz, bc, dt, dh,
                                                 status, partials, p, stream);
 }
+
+extern "C" int gamer_hydro_advance_level_window_mixed(
+    const float* window, float* out, float* face_flux, int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+    int32_t zb, int32_t zn, int32_t z0, int32_t nz, const double* dt, const double* dh,
+    uint32_t* status, double* partials, const gh_params* p, void* stream) {
+    return gamer::hydro_advance_level_window<GAMER_MODE_MIXED>(window, out, face_flux, gx, gy, gz, bc, zb, zn,
+                                                  z0, nz, dt, dh, status, partials, p, stream);
+}

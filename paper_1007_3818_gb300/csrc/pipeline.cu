@@ -1,10 +1,13 @@
-// pipeline.cu -- host-resident batches streamed through the GPU: host->device
+// pipeline.cu -- host-resident data streamed through the GPU: host->device
 // copy, hydro step and device->host copy of successive batches overlap on
 // three streams (the paper overlaps CPU ghost preparation, GPU solves and disk
-// I/O the same way, Sec. 2 and Sec. 3).  The pipeline owns its device buffers
-// (allocated once at creation); advance_host itself allocates nothing.
+// I/O the same way, Sec. 2 and Sec. 3).  Tile batches use the buffers
+// allocated at creation; a host-resident level is streamed in z-slabs of its
+// 16^3 interiors with a one-layer halo on each side, the ghost zones being
+// gathered on the device (window buffers allocated on first use).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -20,6 +23,20 @@ extern "C" int gamer_hydro_advance_mixed(const float*, float*, float*, const dou
 extern "C" int gamer_hydro_advance_f64(const double*, double*, double*, const double*,
                                        const double*, uint32_t*, double*, int64_t,
                                        const gh_params*, void*);
+extern "C" int gamer_hydro_advance_level_window_f32(const float*, float*, float*, int32_t, int32_t,
+                                                    int32_t, int32_t, int32_t, int32_t, int32_t,
+                                                    int32_t, const double*, const double*,
+                                                    uint32_t*, double*, const gh_params*, void*);
+extern "C" int gamer_hydro_advance_level_window_mixed(const float*, float*, float*, int32_t,
+                                                      int32_t, int32_t, int32_t, int32_t, int32_t,
+                                                      int32_t, int32_t, const double*,
+                                                      const double*, uint32_t*, double*,
+                                                      const gh_params*, void*);
+extern "C" int gamer_hydro_advance_level_window_f64(const double*, double*, double*, int32_t,
+                                                    int32_t, int32_t, int32_t, int32_t, int32_t,
+                                                    int32_t, int32_t, const double*,
+                                                    const double*, uint32_t*, double*,
+                                                    const gh_params*, void*);
 
 namespace {
 
@@ -35,15 +52,31 @@ struct BufSet {
     double* partials = nullptr;
     cudaEvent_t h2d_done = nullptr, comp_done = nullptr, d2h_done = nullptr;
     bool used = false;
+    // z-slab window of a host-resident level (level steps only)
+    void* win = nullptr;
+    void* wout = nullptr;
+    double* wdt = nullptr;
+    uint32_t* wstatus = nullptr;
+    double* wpartials = nullptr;
+    size_t win_cap = 0, wout_cap = 0, wn_cap = 0;  // bytes, bytes, groups
 };
 
 }  // namespace
 
 struct gamer_pipeline {
-    // pinned host staging of ghost-padded tiles for level steps (allocated on
-    // the first gamer_pipeline_level_step_host call)
-    void* staging[3] = {nullptr, nullptr, nullptr};
-    double* stage_dt = nullptr;  // pinned [2][batch]: dt, dh of a level step
+    double* stage_dt = nullptr;  // pinned [2][n]: dt, dh of a level step
+    size_t stage_n = 0;
+    // device copy of a whole level (levels that fit): input, output, dt/dh,
+    // status, partials; allocated on first use, grown when needed
+    void* lev_in = nullptr;
+    void* lev_out = nullptr;
+    double* lev_dt = nullptr;
+    uint32_t* lev_status = nullptr;
+    double* lev_partials = nullptr;
+    size_t lev_cap = 0;  // groups
+    cudaEvent_t lev_ev[3] = {nullptr, nullptr, nullptr};
+    int level_mode = 0;  // 0 automatic, 1 device copy of the level, 2 slab windows
+    int64_t h2d_bytes = 0, d2h_bytes = 0;  // copied by the last call
     int mode = 0;
     int64_t batch = 0;
     int with_flux = 0;
@@ -58,9 +91,14 @@ namespace {
 
 void release(gamer_pipeline* pl) {
     if (!pl) return;
-    for (auto& st : pl->staging)
-        if (st) cudaFreeHost(st);
     if (pl->stage_dt) cudaFreeHost(pl->stage_dt);
+    cudaFree(pl->lev_in);
+    cudaFree(pl->lev_out);
+    cudaFree(pl->lev_dt);
+    cudaFree(pl->lev_status);
+    cudaFree(pl->lev_partials);
+    for (auto& ev : pl->lev_ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto& b : pl->set) {
         cudaFree(b.in);
         cudaFree(b.out);
@@ -69,6 +107,11 @@ void release(gamer_pipeline* pl) {
         cudaFree(b.dh);
         cudaFree(b.status);
         cudaFree(b.partials);
+        cudaFree(b.win);
+        cudaFree(b.wout);
+        cudaFree(b.wdt);
+        cudaFree(b.wstatus);
+        cudaFree(b.wpartials);
         if (b.h2d_done) cudaEventDestroy(b.h2d_done);
         if (b.comp_done) cudaEventDestroy(b.comp_done);
         if (b.d2h_done) cudaEventDestroy(b.d2h_done);
@@ -154,6 +197,7 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     if (N < 0) return GAMER_E_PARAM;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
+    pl->h2d_bytes = pl->d2h_bytes = 0;
     if (N == 0) return GAMER_OK;
     if (!in_host || !out_host || !dt_host || !dh_host) return GAMER_E_NULL;
     if (face_flux_host && !pl->with_flux) return GAMER_E_PARAM;
@@ -165,6 +209,10 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     char* hout = static_cast<char*>(out_host);
     char* hff = static_cast<char*>(face_flux_host);
     const int64_t nb = (N + pl->batch - 1) / pl->batch;
+    // bytes this call moves: tiles, dt and dh in; states, fluxes, status, partials out
+    pl->h2d_bytes = N * (40000 * int64_t(e) + 16);
+    pl->d2h_bytes = N * (20480 * int64_t(e) + (hff ? int64_t(ffg) * int64_t(e) : 0) +
+                         (status_host ? 4 : 0) + (partials_host ? 48 : 0));
     for (int64_t b = 0; b < nb; ++b) {
         BufSet& S = pl->set[b % kSets];
         const int64_t g0 = b * pl->batch;
@@ -214,108 +262,320 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     return wait_event(last.d2h_done, pl->timeout_s);
 }
 
-namespace gamer {
-template <class T>
-void fill_tiles_host(const T* level, T* out, int gx, int gy, int gz, int bc, int64_t g0,
-                     int64_t g1, int nthreads);
+namespace {
+
+// (Re)allocates a set's window buffers for win_bytes of input and n groups.
+bool ensure_window(BufSet& S, size_t win_bytes, size_t n, size_t esz) {
+    if (S.win_cap < win_bytes) {
+        cudaFree(S.win);
+        S.win = nullptr;
+        S.win_cap = 0;
+        if (cudaMalloc(&S.win, win_bytes) != cudaSuccess) return false;
+        S.win_cap = win_bytes;
+    }
+    if (S.wn_cap < n) {
+        cudaFree(S.wout);
+        cudaFree(S.wdt);
+        cudaFree(S.wstatus);
+        cudaFree(S.wpartials);
+        S.wout = S.wdt = nullptr;
+        S.wstatus = nullptr;
+        S.wpartials = nullptr;
+        S.wn_cap = S.wout_cap = 0;
+        if (cudaMalloc(&S.wout, n * 20480 * esz) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&S.wdt), n * 16) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&S.wstatus), n * 4) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&S.wpartials), n * 48) != cudaSuccess)
+            return false;
+        S.wn_cap = n;
+        S.wout_cap = n * 20480 * esz;
+    }
+    return true;
 }
 
+// Whether a level of G groups (level_bytes of interiors) is advanced from a
+// device copy of the whole level: when that copy exists already or its input
+// and output fit in 80 % of the free device memory.  Allocates it if so.
+bool level_resident(gamer_pipeline* pl, int64_t G, size_t level_bytes) {
+    if (pl->level_mode == 2) return false;
+    if (pl->lev_cap >= size_t(G)) return true;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t need = 2 * level_bytes + size_t(G) * (16 + 4 + 48);
+    if (pl->level_mode == 0 && double(need) > 0.8 * double(free_b)) return false;
+    cudaFree(pl->lev_in);
+    cudaFree(pl->lev_out);
+    cudaFree(pl->lev_dt);
+    cudaFree(pl->lev_status);
+    cudaFree(pl->lev_partials);
+    pl->lev_in = pl->lev_out = nullptr;
+    pl->lev_dt = pl->lev_partials = nullptr;
+    pl->lev_status = nullptr;
+    pl->lev_cap = 0;
+    bool ok = cudaMalloc(&pl->lev_in, level_bytes) == cudaSuccess &&
+              cudaMalloc(&pl->lev_out, level_bytes) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&pl->lev_dt), size_t(G) * 16) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&pl->lev_status), size_t(G) * 4) ==
+                  cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&pl->lev_partials), size_t(G) * 48) ==
+                  cudaSuccess;
+    for (auto& ev : pl->lev_ev)
+        ok = ok && (ev || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess);
+    if (!ok) {
+        cudaGetLastError();
+        return false;
+    }
+    pl->lev_cap = size_t(G);
+    return true;
+}
+
+// Level step from the device copy: slab s (layers z0 .. z0+nz-1) is copied in
+// on the h2d stream; its kernel, on the compute stream, waits for its own
+// copy and the next slab's (the layer above) and for the periodic wrap layer,
+// which goes first; its results go back on the d2h stream.  Every layer
+// crosses the link once (plus the wrap layer).
+int level_step_resident(gamer_pipeline* pl, const char* hin, char* hout, int32_t gx, int32_t gy,
+                        int32_t gz, int32_t bc, int32_t L, uint32_t* status_host,
+                        double* partials_host, const gh_params* p) {
+    using namespace gamer;
+    const size_t e = pl->esz;
+    const int64_t layer = int64_t(gx) * gy;
+    const int64_t G = layer * gz;
+    const size_t layer_bytes = size_t(layer) * 20480 * e;
+    char* din = static_cast<char*>(pl->lev_in);
+    char* dout = static_cast<char*>(pl->lev_out);
+    // dt, dh of every group: one copy of the pinned staging (filled by the caller)
+    if (cudaMemcpyAsync(pl->lev_dt, pl->stage_dt, size_t(G) * 8, cudaMemcpyHostToDevice,
+                        pl->s_h2d) != cudaSuccess ||
+        cudaMemcpyAsync(pl->lev_dt + G, pl->stage_dt + G, size_t(G) * 8,
+                        cudaMemcpyHostToDevice, pl->s_h2d) != cudaSuccess)
+        return GAMER_E_CUDA;
+    pl->h2d_bytes += 16 * G;
+    const int32_t nslab = (gz + L - 1) / L;
+    // the periodic wrap layer below slab 0 first
+    if (bc == 0 && nslab > 1) {
+        if (cudaMemcpyAsync(din + size_t(gz - 1) * layer_bytes, hin + size_t(gz - 1) * layer_bytes,
+                            layer_bytes, cudaMemcpyHostToDevice, pl->s_h2d) != cudaSuccess)
+            return GAMER_E_CUDA;
+        pl->h2d_bytes += int64_t(layer_bytes);
+    }
+    auto copy_in = [&](int32_t s) -> bool {
+        const int32_t z0 = s * L, nz = std::min<int32_t>(L, gz - z0);
+        size_t off = size_t(z0) * layer_bytes, bytes = size_t(nz) * layer_bytes;
+        if (bc == 0 && nslab > 1 && s == nslab - 1) bytes -= layer_bytes;  // wrap layer: sent
+        pl->h2d_bytes += int64_t(bytes);
+        return (bytes == 0 || cudaMemcpyAsync(din + off, hin + off, bytes, cudaMemcpyHostToDevice,
+                                              pl->s_h2d) == cudaSuccess) &&
+               cudaEventRecord(pl->lev_ev[s % 3], pl->s_h2d) == cudaSuccess;
+    };
+    if (!copy_in(0)) return GAMER_E_CUDA;
+    int rc = GAMER_OK;
+    for (int32_t s = 0; s < nslab; ++s) {
+        // the kernel of slab s reads the first layer of slab s + 1
+        if (s + 1 < nslab && !copy_in(s + 1)) return GAMER_E_CUDA;
+        const cudaEvent_t need = pl->lev_ev[(s + 1 < nslab ? s + 1 : s) % 3];
+        if (cudaStreamWaitEvent(pl->s_comp, need, 0) != cudaSuccess) return GAMER_E_CUDA;
+        const int32_t z0 = s * L, nz = std::min<int32_t>(L, gz - z0);
+        const int64_t g0 = int64_t(z0) * layer, n = int64_t(nz) * layer;
+        char* o = dout + size_t(g0) * 20480 * e;
+        if (pl->mode == GAMER_MODE_F32)
+            rc = gamer_hydro_advance_level_window_f32(
+                (const float*)din, (float*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
+                pl->lev_dt + g0, pl->lev_dt + G + g0, pl->lev_status + g0,
+                pl->lev_partials + g0 * 6, p, pl->s_comp);
+        else if (pl->mode == GAMER_MODE_MIXED)
+            rc = gamer_hydro_advance_level_window_mixed(
+                (const float*)din, (float*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
+                pl->lev_dt + g0, pl->lev_dt + G + g0, pl->lev_status + g0,
+                pl->lev_partials + g0 * 6, p, pl->s_comp);
+        else
+            rc = gamer_hydro_advance_level_window_f64(
+                (const double*)din, (double*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
+                pl->lev_dt + g0, pl->lev_dt + G + g0, pl->lev_status + g0,
+                pl->lev_partials + g0 * 6, p, pl->s_comp);
+        if (rc != GAMER_OK) return rc;
+        BufSet& S = pl->set[s % kSets];
+        bool ok = cudaEventRecord(S.comp_done, pl->s_comp) == cudaSuccess &&
+                  cudaStreamWaitEvent(pl->s_d2h, S.comp_done, 0) == cudaSuccess &&
+                  cudaMemcpyAsync(hout + size_t(g0) * 20480 * e, o, size_t(n) * 20480 * e,
+                                  cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+        pl->d2h_bytes += n * 20480 * int64_t(e);
+        if (ok && status_host) {
+            ok = cudaMemcpyAsync(status_host + g0, pl->lev_status + g0, size_t(n) * 4,
+                                 cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+            pl->d2h_bytes += 4 * n;
+        }
+        if (ok && partials_host) {
+            ok = cudaMemcpyAsync(partials_host + g0 * 6, pl->lev_partials + g0 * 6,
+                                 size_t(n) * 48, cudaMemcpyDeviceToHost, pl->s_d2h) ==
+                 cudaSuccess;
+            pl->d2h_bytes += 48 * n;
+        }
+        ok = ok && cudaEventRecord(S.d2h_done, pl->s_d2h) == cudaSuccess;
+        if (!ok) return GAMER_E_CUDA;
+        S.used = true;
+    }
+    return wait_event(pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
+}
+
+}  // namespace
+
+// A host-resident level in z-slabs of L layers (L*gx*gy ~ the batch size):
+// each slab's window -- its layers plus the layer below and above (periodic
+// wrap or zero-gradient clamp) -- goes to the device in at most two copies,
+// the window kernel advances the slab with the ghost zones gathered on the
+// device, and the slab's results come back; three slabs are in flight.
 extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* level_in_host,
                                               void* level_out_host, int32_t gx, int32_t gy,
                                               int32_t gz, int32_t bc, double dt, double dh,
                                               uint32_t* status_host, double* partials_host,
-                                              const gh_params* p, int32_t nthreads) {
+                                              const gh_params* p, int32_t /*nthreads*/) {
     using namespace gamer;
     if (!pl) return GAMER_E_NULL;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
     if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1)) return GAMER_E_PARAM;
-    const int64_t G = int64_t(gx) * gy * gz;
+    pl->h2d_bytes = pl->d2h_bytes = 0;
+    const int64_t layer = int64_t(gx) * gy;
+    const int64_t G = layer * gz;
     if (G == 0) return GAMER_OK;
     if (!level_in_host || !level_out_host) return GAMER_E_NULL;
     if (level_in_host == level_out_host) return GAMER_E_OVERLAP;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return GAMER_E_DEVICE;
     const size_t e = pl->esz;
-    const size_t tile_bytes = size_t(pl->batch) * 40000 * e;
-    if (!pl->staging[0]) {
-        for (auto& st : pl->staging)
-            if (cudaHostAlloc(&st, tile_bytes, cudaHostAllocDefault) != cudaSuccess) {
-                cudaGetLastError();
-                return GAMER_E_CUDA;
-            }
-        if (cudaHostAlloc(reinterpret_cast<void**>(&pl->stage_dt), size_t(pl->batch) * 16,
+    const size_t layer_bytes = size_t(layer) * 20480 * e;
+    const int32_t L = int32_t(std::max<int64_t>(1, std::min<int64_t>(pl->batch / layer, gz)));
+    const int32_t zn_max = std::min<int32_t>(L + 2, gz);
+    const size_t n_max = size_t(L) * size_t(layer);
+    const bool resident = level_resident(pl, G, layer_bytes * size_t(gz));
+    // pinned dt, dh staging: [2][cnt], cnt = the groups of one copy
+    const size_t cnt = resident ? size_t(G) : n_max;
+    if (pl->stage_n < cnt) {
+        if (pl->stage_dt) cudaFreeHost(pl->stage_dt);
+        pl->stage_dt = nullptr;
+        pl->stage_n = 0;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pl->stage_dt), cnt * 16,
                           cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             return GAMER_E_CUDA;
         }
+        pl->stage_n = cnt;
     }
     // every group of the level takes the same dt and dh
-    for (int64_t i = 0; i < pl->batch; ++i) {
+    for (size_t i = 0; i < cnt; ++i) {
         pl->stage_dt[i] = dt;
-        pl->stage_dt[pl->batch + i] = dh;
+        pl->stage_dt[cnt + i] = dh;
     }
-    const double* hdt = pl->stage_dt;
-    const double* hdh = pl->stage_dt + pl->batch;
+    const char* hin = static_cast<const char*>(level_in_host);
     char* hout = static_cast<char*>(level_out_host);
-    const int64_t nb = (G + pl->batch - 1) / pl->batch;
-    for (int64_t b = 0; b < nb; ++b) {
-        BufSet& S = pl->set[b % kSets];
-        char* stg = static_cast<char*>(pl->staging[b % kSets]);
-        const int64_t g0 = b * pl->batch;
-        const int64_t n = std::min<int64_t>(pl->batch, G - g0);
-        // the staging buffer is refilled only once its previous copy has left
-        if (S.used && (rc = wait_event(S.h2d_done, pl->timeout_s)) != GAMER_OK) return rc;
-        // host ghost preparation of this batch overlaps the GPU work queued before it
-        if (pl->mode == GAMER_MODE_F64)
-            fill_tiles_host<double>(static_cast<const double*>(level_in_host),
-                                    reinterpret_cast<double*>(stg), gx, gy, gz, bc, g0, g0 + n,
-                                    nthreads);
-        else
-            fill_tiles_host<float>(static_cast<const float*>(level_in_host),
-                                   reinterpret_cast<float*>(stg), gx, gy, gz, bc, g0, g0 + n,
-                                   nthreads);
-        if (S.used && cudaStreamWaitEvent(pl->s_h2d, S.d2h_done, 0) != cudaSuccess)
+    const int32_t nslab = (gz + L - 1) / L;
+    if (resident)
+        return level_step_resident(pl, hin, hout, gx, gy, gz, bc, L, status_host,
+                                   partials_host, p);
+    for (int32_t sl = 0; sl < nslab; ++sl) {
+        BufSet& S = pl->set[sl % kSets];
+        const int32_t z0 = sl * L, nz = std::min<int32_t>(L, gz - z0);
+        const int64_t n = int64_t(nz) * layer;
+        int32_t zb, zn;
+        if (bc == 0) {
+            zn = std::min<int32_t>(nz + 2, gz);
+            zb = (zn == gz) ? 0 : (z0 - 1 + gz) % gz;
+        } else {
+            const int32_t lo = std::max<int32_t>(z0 - 1, 0), hi = std::min<int32_t>(z0 + nz, gz - 1);
+            zb = lo;
+            zn = hi - lo + 1;
+        }
+        // the set's buffers are reused only once its previous results have left
+        if (S.used && (rc = wait_event(S.d2h_done, pl->timeout_s)) != GAMER_OK) return rc;
+        if (!ensure_window(S, size_t(zn_max) * layer_bytes, n_max, e)) {
+            cudaGetLastError();
             return GAMER_E_CUDA;
-        bool ok = cudaMemcpyAsync(S.in, stg, size_t(n) * 40000 * e, cudaMemcpyHostToDevice,
-                                  pl->s_h2d) == cudaSuccess &&
-                  cudaMemcpyAsync(S.dt, hdt, size_t(n) * 8, cudaMemcpyHostToDevice,
-                                  pl->s_h2d) == cudaSuccess &&
-                  cudaMemcpyAsync(S.dh, hdh, size_t(n) * 8, cudaMemcpyHostToDevice,
-                                  pl->s_h2d) == cudaSuccess &&
-                  cudaEventRecord(S.h2d_done, pl->s_h2d) == cudaSuccess &&
-                  cudaStreamWaitEvent(pl->s_comp, S.h2d_done, 0) == cudaSuccess;
+        }
+        // window layers zb .. zb+zn-1 (mod gz): one copy, or two across the wrap
+        const int32_t first = std::min<int32_t>(zn, gz - zb);
+        bool ok = cudaMemcpyAsync(S.win, hin + size_t(zb) * layer_bytes, size_t(first) * layer_bytes,
+                                  cudaMemcpyHostToDevice, pl->s_h2d) == cudaSuccess;
+        if (ok && first < zn)
+            ok = cudaMemcpyAsync(static_cast<char*>(S.win) + size_t(first) * layer_bytes, hin,
+                                 size_t(zn - first) * layer_bytes, cudaMemcpyHostToDevice,
+                                 pl->s_h2d) == cudaSuccess;
+        ok = ok &&
+             cudaMemcpyAsync(S.wdt, pl->stage_dt, size_t(n) * 8, cudaMemcpyHostToDevice,
+                             pl->s_h2d) == cudaSuccess &&
+             cudaMemcpyAsync(S.wdt + n, pl->stage_dt + n_max, size_t(n) * 8,
+                             cudaMemcpyHostToDevice, pl->s_h2d) == cudaSuccess &&
+             cudaEventRecord(S.h2d_done, pl->s_h2d) == cudaSuccess &&
+             cudaStreamWaitEvent(pl->s_comp, S.h2d_done, 0) == cudaSuccess;
         if (!ok) return GAMER_E_CUDA;
+        pl->h2d_bytes += int64_t(zn) * int64_t(layer_bytes) + 16 * n;
         if (pl->mode == GAMER_MODE_F32)
-            rc = gamer_hydro_advance_f32((const float*)S.in, (float*)S.out, nullptr, S.dt, S.dh,
-                                         S.status, S.partials, n, p, pl->s_comp);
+            rc = gamer_hydro_advance_level_window_f32(
+                (const float*)S.win, (float*)S.wout, nullptr, gx, gy, gz, bc, zb, zn, z0, nz,
+                S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
         else if (pl->mode == GAMER_MODE_MIXED)
-            rc = gamer_hydro_advance_mixed((const float*)S.in, (float*)S.out, nullptr, S.dt,
-                                           S.dh, S.status, S.partials, n, p, pl->s_comp);
+            rc = gamer_hydro_advance_level_window_mixed(
+                (const float*)S.win, (float*)S.wout, nullptr, gx, gy, gz, bc, zb, zn, z0, nz,
+                S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
         else
-            rc = gamer_hydro_advance_f64((const double*)S.in, (double*)S.out, nullptr, S.dt,
-                                         S.dh, S.status, S.partials, n, p, pl->s_comp);
+            rc = gamer_hydro_advance_level_window_f64(
+                (const double*)S.win, (double*)S.wout, nullptr, gx, gy, gz, bc, zb, zn, z0, nz,
+                S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
         if (rc != GAMER_OK) return rc;
+        const int64_t g0 = int64_t(z0) * layer;
         ok = cudaEventRecord(S.comp_done, pl->s_comp) == cudaSuccess &&
              cudaStreamWaitEvent(pl->s_d2h, S.comp_done, 0) == cudaSuccess &&
-             cudaMemcpyAsync(hout + size_t(g0) * 20480 * e, S.out, size_t(n) * 20480 * e,
+             cudaMemcpyAsync(hout + size_t(g0) * 20480 * e, S.wout, size_t(n) * 20480 * e,
                              cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
-        if (ok && status_host)
-            ok = cudaMemcpyAsync(status_host + g0, S.status, size_t(n) * 4,
+        pl->d2h_bytes += n * 20480 * int64_t(e);
+        if (ok && status_host) {
+            ok = cudaMemcpyAsync(status_host + g0, S.wstatus, size_t(n) * 4,
                                  cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
-        if (ok && partials_host)
-            ok = cudaMemcpyAsync(partials_host + g0 * 6, S.partials, size_t(n) * 48,
+            pl->d2h_bytes += 4 * n;
+        }
+        if (ok && partials_host) {
+            ok = cudaMemcpyAsync(partials_host + g0 * 6, S.wpartials, size_t(n) * 48,
                                  cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess;
+            pl->d2h_bytes += 48 * n;
+        }
         ok = ok && cudaEventRecord(S.d2h_done, pl->s_d2h) == cudaSuccess;
         if (!ok) return GAMER_E_CUDA;
         S.used = true;
     }
-    return wait_event(pl->set[(nb - 1) % kSets].d2h_done, pl->timeout_s);
+    return wait_event(pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
+}
+
+extern "C" int gamer_pipeline_last_bytes(const gamer_pipeline* pl, int64_t* h2d, int64_t* d2h) {
+    if (!pl || !h2d || !d2h) return GAMER_E_NULL;
+    *h2d = pl->h2d_bytes;
+    *d2h = pl->d2h_bytes;
+    return GAMER_OK;
 }
 
 extern "C" int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds) {
     if (!pl) return GAMER_E_NULL;
     if (!(seconds > 0.0)) return GAMER_E_PARAM;
     pl->timeout_s = seconds;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_pipeline_set_level_mode(gamer_pipeline* pl, int32_t mode) {
+    if (!pl) return GAMER_E_NULL;
+    if (mode < 0 || mode > 2) return GAMER_E_PARAM;
+    pl->level_mode = mode;
+    if (mode == 2) {  // give the device copy back
+        cudaFree(pl->lev_in);
+        cudaFree(pl->lev_out);
+        cudaFree(pl->lev_dt);
+        cudaFree(pl->lev_status);
+        cudaFree(pl->lev_partials);
+        pl->lev_in = pl->lev_out = nullptr;
+        pl->lev_dt = pl->lev_partials = nullptr;
+        pl->lev_status = nullptr;
+        pl->lev_cap = 0;
+    }
     return GAMER_OK;
 }

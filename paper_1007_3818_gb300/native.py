@@ -69,6 +69,12 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, P(gh_params), vp]
             f.restype = ctypes.c_int
+        for name in ("gamer_hydro_advance_level_window_f32", "gamer_hydro_advance_level_window_mixed",
+                     "gamer_hydro_advance_level_window_f64"):
+            f = getattr(L, name)
+            f.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp,
+                          P(gh_params), vp]
+            f.restype = ctypes.c_int
         for name in ("gamer_fill_ghosts_uniform_f32", "gamer_fill_ghosts_uniform_f64"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, i32, i32, i32, i32, vp]
@@ -118,6 +124,10 @@ def lib():
         L.gamer_pipeline_level_step_host.argtypes = [vp, vp, vp, i32, i32, i32, i32, d, d, vp, vp,
                                                      P(gh_params), i32]
         L.gamer_pipeline_level_step_host.restype = ctypes.c_int
+        L.gamer_pipeline_last_bytes.argtypes = [vp, P(i64), P(i64)]
+        L.gamer_pipeline_last_bytes.restype = ctypes.c_int
+        L.gamer_pipeline_set_level_mode.argtypes = [vp, i32]
+        L.gamer_pipeline_set_level_mode.restype = ctypes.c_int
         for name in ("gamer_fill_ghosts_uniform_host_f32", "gamer_fill_ghosts_uniform_host_f64"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, i32, i32, i32, i32, i32]
@@ -227,6 +237,34 @@ def hydro_advance_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, sta
             _ptr(status, torch.int32, (), "status"), _ptr(partials, torch.float64, (6,), "partials")]
     rc = getattr(lib(), _ADV_LEVEL[mode])(*args, ctypes.byref(params), _stream(stream))
     _check(rc, _ADV_LEVEL[mode])
+
+
+def hydro_advance_level_window(mode, window, out, face_flux, gx, gy, gz, bc, zb, z0, nz, dt, dh,
+                               status, partials, params, stream=None):
+    """Layers z0 .. z0+nz-1 of a gx*gy*gz level from a device window
+    [zn*gx*gy, 5, 16, 16, 16] holding level layers zb, zb+1, ... (mod gz)."""
+    import torch
+    T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+    layer = gx * gy
+    if layer == 0 or int(window.shape[0]) % layer:
+        raise GamerError(-2, "window must hold whole layers of gx*gy groups")
+    zn = int(window.shape[0]) // layer
+    N = layer * nz
+    for t, nm in ((out, "out"), (face_flux, "face_flux"), (dt, "dt"), (dh, "dh"),
+                  (status, "status"), (partials, "partials")):
+        if t is not None and int(t.shape[0]) != N:
+            raise GamerError(-2, f"{nm} must hold gx*gy*nz = {N} groups")
+    name = {GAMER_MODE_F32: "gamer_hydro_advance_level_window_f32",
+            GAMER_MODE_MIXED: "gamer_hydro_advance_level_window_mixed",
+            GAMER_MODE_F64: "gamer_hydro_advance_level_window_f64"}[mode]
+    rc = getattr(lib(), name)(
+        _ptr(window, T, (5, 16, 16, 16), "window"), _ptr(out, T, (5, 16, 16, 16), "out"),
+        _ptr(face_flux, T, (FLUX_PLANES[params.flux_layout], 5, 16, 16), "face_flux"),
+        int(gx), int(gy), int(gz), int(bc), int(zb), zn, int(z0), int(nz),
+        _ptr(dt, torch.float64, (), "dt"), _ptr(dh, torch.float64, (), "dh"),
+        _ptr(status, torch.int32, (), "status"), _ptr(partials, torch.float64, (6,), "partials"),
+        ctypes.byref(params), _stream(stream))
+    _check(rc, name)
 
 
 def gamer_hydro_advance_level_f32(level, out, face_flux, gx, gy, gz, bc, dt, dh, status,
@@ -475,6 +513,18 @@ class Pipeline:
                                                   p(partials), ctypes.byref(params),
                                                   int(nthreads))
         _check(rc, "gamer_pipeline_level_step_host")
+
+    def set_level_mode(self, mode):
+        """0 automatic, 1 device copy of the whole level, 2 slab windows."""
+        _check(lib().gamer_pipeline_set_level_mode(self.handle, int(mode)),
+               "gamer_pipeline_set_level_mode")
+
+    def last_bytes(self):
+        """(host->device, device->host) bytes copied by the last call."""
+        h2d, d2h = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().gamer_pipeline_last_bytes(self.handle, ctypes.byref(h2d), ctypes.byref(d2h)),
+               "gamer_pipeline_last_bytes")
+        return int(h2d.value), int(d2h.value)
 
     def close(self):
         if self.handle:

@@ -116,6 +116,26 @@ def test_advance_level_rejects_bad_arguments(lib, name):
     assert call(out=FAKE + 4096) == -6                # out inside the level
 
 
+@pytest.mark.parametrize("name", ["gamer_hydro_advance_level_window_f32",
+                                  "gamer_hydro_advance_level_window_f64"])
+def test_level_window_rejects_missing_layers(lib, name):
+    f = getattr(lib, name)
+    prm = native.make_params(1.4)
+    GB = 1 << 32
+
+    def call(gz=8, bc=0, zb=0, zn=8, z0=0, nz=8):
+        return f(P(FAKE), P(FAKE + GB), None, 2, 2, gz, bc, zb, zn, z0, nz, P(FAKE + 2 * GB),
+                 P(FAKE + 3 * GB), None, None, ctypes.byref(prm), None)
+
+    # only calls that fail validation (never reach the device with these fake pointers)
+    assert call(nz=0) == 0                           # nothing to do
+    assert call(z0=6, nz=3) == -2                    # beyond the level
+    assert call(zb=8) == -2 and call(zn=9) == -2
+    assert call(zb=3, zn=3, z0=3, nz=2) == -2        # needs 2..5: layer 2 below is missing
+    assert call(zb=2, zn=3, z0=3, nz=2) == -2        # needs 2..5: layer 5 above is missing
+    assert call(zb=0, zn=2, z0=0, nz=1, bc=0) == -2  # periodic: layer 7 below is missing
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_flux_fixup_and_restrict_reject_bad_arguments(lib, prec):
     fix = getattr(lib, f"gamer_flux_fixup_{prec}")

@@ -157,10 +157,11 @@ def test_amr_batch_full_size_sampled(mode, tol):
     assert (dt_level.cpu().numpy() > 0).all()
 
 
+@pytest.mark.parametrize("level_mode", [1, 2], ids=["device-copy", "slab-windows"])
 @pytest.mark.parametrize("mode,tol", [(F32, TOL_F32_1), (F64, TOL_F64)], ids=["f32", "f64"])
-def test_pipeline_level_step_small(mode, tol):
-    """Host-resident level through the streamed pipeline (host ghost fill +
-    H2D / step / D2H overlap), batches that do not divide the level."""
+def test_pipeline_level_step_small(mode, tol, level_mode):
+    """Host-resident level through the streamed pipeline (z-slabs with halo
+    layers, ghost zones gathered on the device, H2D / step / D2H overlap)."""
     import torch
     from paper_1007_3818_gb300 import native
     g, dh, dt = 5 / 3, 1 / 64, 1.5e-3
@@ -173,8 +174,19 @@ def test_pipeline_level_step_small(mode, tol):
     part = torch.zeros((64, 6), dtype=torch.float64).pin_memory()
     st = torch.zeros(64, dtype=torch.int32).pin_memory()
     pl = native.Pipeline(mode, 24, with_flux=False)
+    pl.set_level_mode(level_mode)
     pl.level_step_host(h_in, h_out, 4, 4, 4, 0, dt, dh, st, part, native.make_params(g))
+    h2d, d2h = pl.last_bytes()
     pl.close()
+    esz = 8 if mode == F64 else 4
+    if level_mode == 2:
+        # slabs of one layer (16 groups <= 24): each sends its layer and both neighbours
+        assert h2d == 4 * (3 * 16 * 20480 * esz + 16 * 16)
+    else:
+        # every layer once (the periodic wrap layer goes first, not again at
+        # the end), and dt, dh of all groups
+        assert h2d == 4 * 16 * 20480 * esz + 16 * 64
+    assert d2h == 64 * (20480 * esz + 4 + 48)
     tiles = oracle.fill_ghosts_uniform(lv, 4, 4, 4, 0)
     r_out, _, r_st, r_part = oracle.advance_groups(tiles, dt, dh, gamma=g, want_flux=False)
     assert rel_l1_fields(h_out.double().numpy(), r_out) <= tol
@@ -182,9 +194,10 @@ def test_pipeline_level_step_small(mode, tol):
 
 
 def test_streamed_level_full_size_sampled():
-    """Config 5: a 1024^3 level (64^3 = 262,144 groups, 42 GB of FP32 tiles
-    per step) held in pinned host memory, one streamed step (host ghost fill
-    overlapped with H2D / step / D2H on 3 streams); 24 sampled groups checked.
+    """Config 5: a 1024^3 level (64^3 = 262,144 groups, 21 GB of FP32
+    interiors) held in pinned host memory, one streamed step (z-slabs with halo
+    layers, ghost gather on the device, H2D / step / D2H overlapped on 3
+    streams); 24 sampled groups checked.
     The level tiles a periodic 256^3 lognormal field of density contrast 1e4,
     so each group's ghost-padded input is that of a group of the 256^3 field."""
     import torch

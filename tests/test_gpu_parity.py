@@ -513,6 +513,55 @@ def _fused_vs_fill(mode, bc, dims):
     assert rel_l1_fields(a[0].astype(np.float64), r_out) <= (TOL_F64 if mode == F64 else TOL_F32_1)
 
 
+@pytest.mark.parametrize("mode", [F32, F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_level_window_equals_full_level(mode, bc):
+    """Slabs of a level advanced from device windows (the layers they read,
+    wrapped or clamped) equal the whole-level step bit for bit."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    gx, gy, gz = 3, 2, 5
+    layer, G = gx * gy, gx * gy * gz
+    rng = np.random.default_rng(17 + bc)
+    lv = np.concatenate([wl.level_to_groups(wl.fourier_level(n=16, seed=int(s), gamma=g))
+                         for s in rng.integers(1 << 30, size=G)])
+    T = torch_dtype(mode)
+    d_lv = torch.from_numpy(lv).to("cuda", T)
+    p = native.make_params(g)
+
+    def vec(v, n):
+        return torch.full((n,), v, device="cuda", dtype=torch.float64)
+
+    full = torch.empty_like(d_lv)
+    st_full = torch.zeros(G, device="cuda", dtype=torch.int32)
+    part_full = torch.zeros((G, 6), device="cuda", dtype=torch.float64)
+    native.hydro_advance_level(mode, d_lv, full, None, gx, gy, gz, bc, vec(2e-3, G),
+                               vec(1 / 64, G), st_full, part_full, p)
+    for z0, nz, whole in ((0, 1, False), (0, 2, False), (2, 3, False), (4, 1, False),
+                          (1, 4, False), (3, 2, True)):
+        if whole:
+            zb, zn = 0, gz
+        elif bc == 0:
+            zn = min(nz + 2, gz)
+            zb = 0 if zn == gz else (z0 - 1) % gz
+        else:
+            lo, hi = max(z0 - 1, 0), min(z0 + nz, gz - 1)
+            zb, zn = lo, hi - lo + 1
+        layers = [(zb + l) % gz for l in range(zn)]
+        win = torch.cat([d_lv[z * layer:(z + 1) * layer] for z in layers]).contiguous()
+        n = nz * layer
+        out = torch.full((n, 5, 16, 16, 16), float("nan"), device="cuda", dtype=T)
+        st = torch.full((n,), -1, device="cuda", dtype=torch.int32)
+        part = torch.zeros((n, 6), device="cuda", dtype=torch.float64)
+        native.hydro_advance_level_window(mode, win, out, None, gx, gy, gz, bc, zb, z0, nz,
+                                          vec(2e-3, n), vec(1 / 64, n), st, part, p)
+        torch.cuda.synchronize()
+        sl = slice(z0 * layer, (z0 + nz) * layer)
+        assert torch.equal(out, full[sl]), (z0, nz, whole)
+        assert torch.equal(st, st_full[sl]) and torch.equal(part, part_full[sl])
+
+
 def test_fused_level_rejects_in_place_update():
     import torch
     from paper_1007_3818_gb300 import native
