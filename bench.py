@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["f32", "mixed", "f64"], default="f32")
+    ap.add_argument("--mode", choices=["f32", "mixed", "f64", "ff"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -254,7 +254,7 @@ def streamed_main(args):
     from paper_1007_3818_gb300 import workloads as wl
     torch.cuda.set_device(0)
     mode = {"f32": native.GAMER_MODE_F32, "mixed": native.GAMER_MODE_MIXED,
-            "f64": native.GAMER_MODE_F64}[args.mode]
+            "f64": native.GAMER_MODE_F64, "ff": native.GAMER_MODE_FF}[args.mode]
     T = torch.float64 if mode == native.GAMER_MODE_F64 else torch.float32
     base = wl.level_to_groups(wl.lognormal_base(256, SEED + 2, gamma=GAMMA,
                                                 sigma_ln=np.log(1e4) / 8, clip=4.0, vel_rms=1.0))
@@ -320,7 +320,7 @@ def main():
     if rc != 0:
         raise SystemExit(f"device check failed: {native.strerror(rc)}")
     mode = {"f32": native.GAMER_MODE_F32, "mixed": native.GAMER_MODE_MIXED,
-            "f64": native.GAMER_MODE_F64}[args.mode]
+            "f64": native.GAMER_MODE_F64, "ff": native.GAMER_MODE_FF}[args.mode]
     T = torch.float64 if mode == native.GAMER_MODE_F64 else torch.float32
     esz = 8 if T == torch.float64 else 4
     gx = gy = gz = NCELLS // 16
@@ -498,7 +498,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f32": "f32", "mixed": "f32+f64", "f64": "f64"}[args.mode],
+            "dtype": {"f32": "f32", "mixed": "f32+f64", "f64": "f64", "ff": "f32"}[args.mode],
             "data": "synthetic",
             "config": {"workload": "uniform periodic level, 4096 patch groups of 16^3 cells "
                                    "(256^3), MUSCL-Hancock/Roe step with the ghost gather "

@@ -59,6 +59,7 @@ extern "C" {
 #define GAMER_MODE_F32 0   /* FP32 storage and arithmetic                                     */
 #define GAMER_MODE_MIXED 1 /* FP32 storage/arithmetic, pressure E - |m|^2/(2 rho) in FP64     */
 #define GAMER_MODE_F64 2   /* FP64 storage and arithmetic                                     */
+#define GAMER_MODE_FF 3    /* FP32 storage/arithmetic, pressure recovery in float-float        */
 
 /* ---- scheme parameters ---- */
 typedef struct gh_params {
@@ -114,14 +115,21 @@ typedef struct gh_params {
  *   N         number of groups (>= 0).
  *   p         scheme parameters (host pointer).
  *   stream    cudaStream_t.
- * _f32 and _mixed take float arrays, _f64 double arrays.  In _mixed mode every
- * recovery of the pressure from the conserved state (where E - rho v^2/2
- * cancels in high-Mach cells) is done in FP64; everything else in FP32.
+ * _f32, _mixed and _ff take float arrays, _f64 double arrays.  In _mixed mode
+ * every recovery of the pressure from the conserved state (where E - rho v^2/2
+ * cancels in high-Mach cells) is done in FP64; everything else in FP32.  _ff
+ * does the same recoveries (and the rho E - |m|^2/2 > 0 tests) in float-float
+ * FP32 arithmetic: |m|^2 exact by FMA products and TwoSum, 1/rho refined to
+ * about 2^-46, E - |m|^2/(2 rho) by TwoSum -- as accurate as the FP64 recovery
+ * for FP32 states while |m|^2/(2 rho) < 2^22 p, at FP32 speed.
  */
 int gamer_hydro_advance_f32(const float* in, float* out, float* face_flux, const double* dt,
                             const double* dh, uint32_t* status, double* partials, int64_t N,
                             const gh_params* p, void* stream);
 int gamer_hydro_advance_mixed(const float* in, float* out, float* face_flux, const double* dt,
+                              const double* dh, uint32_t* status, double* partials, int64_t N,
+                              const gh_params* p, void* stream);
+int gamer_hydro_advance_ff(const float* in, float* out, float* face_flux, const double* dt,
                               const double* dh, uint32_t* status, double* partials, int64_t N,
                               const gh_params* p, void* stream);
 int gamer_hydro_advance_f64(const double* in, double* out, double* face_flux, const double* dt,
@@ -154,6 +162,10 @@ int gamer_hydro_advance_level_mixed(const float* level, float* out, float* face_
                                     int32_t gx, int32_t gy, int32_t gz, int32_t bc,
                                     const double* dt, const double* dh, uint32_t* status,
                                     double* partials, const gh_params* p, void* stream);
+int gamer_hydro_advance_level_ff(const float* level, float* out, float* face_flux,
+                                    int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                    const double* dt, const double* dh, uint32_t* status,
+                                    double* partials, const gh_params* p, void* stream);
 int gamer_hydro_advance_level_f64(const double* level, double* out, double* face_flux,
                                   int32_t gx, int32_t gy, int32_t gz, int32_t bc,
                                   const double* dt, const double* dh, uint32_t* status,
@@ -181,6 +193,11 @@ int gamer_hydro_advance_level_window_f32(const float* window, float* out, float*
                                          const double* dt, const double* dh, uint32_t* status,
                                          double* partials, const gh_params* p, void* stream);
 int gamer_hydro_advance_level_window_mixed(const float* window, float* out, float* face_flux,
+                                           int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                           int32_t zb, int32_t zn, int32_t z0, int32_t nz,
+                                           const double* dt, const double* dh, uint32_t* status,
+                                           double* partials, const gh_params* p, void* stream);
+int gamer_hydro_advance_level_window_ff(const float* window, float* out, float* face_flux,
                                            int32_t gx, int32_t gy, int32_t gz, int32_t bc,
                                            int32_t zb, int32_t zn, int32_t z0, int32_t nz,
                                            const double* dt, const double* dh, uint32_t* status,

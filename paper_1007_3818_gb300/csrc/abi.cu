@@ -40,8 +40,8 @@ int& hydro_variant() {
 }
 
 int& hydro_ctas_per_sm_override(int mode) {
-    static int v[3] = {0, 0, 0};
-    return v[(mode >= 0 && mode < 3) ? mode : 0];
+    static int v[4] = {0, 0, 0, 0};
+    return v[(mode >= 0 && mode < 4) ? mode : 0];
 }
 
 }  // namespace gamer
@@ -68,7 +68,7 @@ extern "C" const char* gamer_version(void) {
 }
 
 extern "C" int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm) {
-    if (mode < 0 || mode > 2 || ctas_per_sm < 0 || ctas_per_sm > 16) return GAMER_E_PARAM;
+    if (mode < 0 || mode > 3 || ctas_per_sm < 0 || ctas_per_sm > 16) return GAMER_E_PARAM;
     gamer::hydro_ctas_per_sm_override(mode) = ctas_per_sm;
     return GAMER_OK;
 }

@@ -47,6 +47,32 @@ template <int MODE> struct Prec;
 template <> struct Prec<GAMER_MODE_F32> { using T = float; using P = float; };
 template <> struct Prec<GAMER_MODE_MIXED> { using T = float; using P = double; };
 template <> struct Prec<GAMER_MODE_F64> { using T = double; using P = double; };
+template <> struct Prec<GAMER_MODE_FF> { using T = float; using P = float; };
+
+// Error-free transformations for the float-float mode: Knuth's TwoSum and the
+// rounding error of a product from one FMA.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+    return s;
+}
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+    const float p = a * b;
+    e = fmaf(a, b, -p);
+    return p;
+}
+
+// |m|^2 as a float-float pair s + se (the squares exact, their sums with
+// TwoSum); accurate to about 2^-47 relative.
+__device__ __forceinline__ float sq3_ff(float m1, float m2, float m3, float& se) {
+    float e1, e2, e3, t1, t2;
+    float s = two_prod(m1, m1, e1);
+    s = two_sum(s, two_prod(m2, m2, e2), t1);
+    s = two_sum(s, two_prod(m3, m3, e3), t2);
+    se = ((e1 + e2) + e3) + (t1 + t2);
+    return s;
+}
 
 template <class T, int RING = 2>
 struct alignas(16) Smem {
@@ -95,6 +121,18 @@ __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KC
         const double a = m1, b = m2, c = m3;
         const double ke = 0.5 * (a * a + b * b + c * c) * ird;
         return static_cast<T>(kc.gm1p * (static_cast<double>(E) - ke));
+    } else if constexpr (MODE == GAMER_MODE_FF) {
+        // the same recovery in float-float: 1/rho = ir (1 + d), d = 1 - rho ir
+        // from one FMA; |m|^2 ir exactly as p + pe; E - ke by TwoSum
+        float se;
+        const float s = sq3_ff(m1, m2, m3, se);
+        const float il = ir * fmaf(-r, ir, 1.0f);
+        float pe;
+        const float p = two_prod(s, ir, pe);
+        const float kh = 0.5f * p, kl = 0.5f * (pe + fmaf(s, il, se * ir));
+        float de;
+        const float d = two_sum(E, -kh, de);
+        return kc.gm1 * (d + (de - kl));
     } else {
         return kc.gm1 * (E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
     }
@@ -142,6 +180,12 @@ __device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
     if constexpr (MODE == GAMER_MODE_MIXED) {
         const double a = m1, b = m2, c = m3;
         return r > T(0) && (double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0;
+    } else if constexpr (MODE == GAMER_MODE_FF) {
+        float se, ee, t;
+        const float s = sq3_ff(m1, m2, m3, se);
+        const float re = two_prod(r, E, ee);
+        const float d = two_sum(re, -0.5f * s, t);
+        return r > 0.0f && (d + ((ee - 0.5f * se) + t)) > 0.0f;
     } else {
         return r > T(0) && (r * E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3)) > T(0);
     }

@@ -16,6 +16,9 @@ extern "C" int gamer_hydro_advance_f32(const float*, float*, float*, const doubl
 extern "C" int gamer_hydro_advance_mixed(const float*, float*, float*, const double*,
                                          const double*, uint32_t*, double*, int64_t,
                                          const gh_params*, void*);
+extern "C" int gamer_hydro_advance_ff(const float*, float*, float*, const double*,
+                                         const double*, uint32_t*, double*, int64_t,
+                                         const gh_params*, void*);
 extern "C" int gamer_hydro_advance_f64(const double*, double*, double*, const double*,
                                        const double*, uint32_t*, double*, int64_t,
                                        const gh_params*, void*);
@@ -41,6 +44,9 @@ int enqueue_step(int mode, const void* cur, void* nxt, void* tiles, void* ff, do
             rc = gamer_hydro_advance_level_mixed((const float*)cur, (float*)nxt, (float*)ff, gx,
                                                  gy, gz, bc, dt_group, dh_group, status, partials,
                                                  p, s);
+        else if (mode == GAMER_MODE_FF)
+            rc = gamer_hydro_advance_level_ff((const float*)cur, (float*)nxt, (float*)ff, gx, gy,
+                                              gz, bc, dt_group, dh_group, status, partials, p, s);
         else
             rc = gamer_hydro_advance_level_f64((const double*)cur, (double*)nxt, (double*)ff, gx,
                                                gy, gz, bc, dt_group, dh_group, status, partials,
@@ -60,6 +66,9 @@ int enqueue_step(int mode, const void* cur, void* nxt, void* tiles, void* ff, do
     else if (mode == GAMER_MODE_MIXED)
         rc = gamer_hydro_advance_mixed((const float*)tiles, (float*)nxt, (float*)ff, dt_group,
                                        dh_group, status, partials, G, p, s);
+    else if (mode == GAMER_MODE_FF)
+        rc = gamer_hydro_advance_ff((const float*)tiles, (float*)nxt, (float*)ff, dt_group,
+                                    dh_group, status, partials, G, p, s);
     else
         rc = gamer_hydro_advance_f64((const double*)tiles, (double*)nxt, (double*)ff, dt_group,
                                      dh_group, status, partials, G, p, s);
@@ -80,7 +89,7 @@ extern "C" int gamer_level_graph_create(int32_t mode, void* level_a, void* level
     using namespace gamer;
     if (!out) return GAMER_E_NULL;
     *out = nullptr;
-    if (mode < 0 || mode > 2 || gx < 1 || gy < 1 || gz < 1) return GAMER_E_PARAM;
+    if (mode < 0 || mode > 3 || gx < 1 || gy < 1 || gz < 1) return GAMER_E_PARAM;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
     if (!(std::isfinite(p->cfl) && p->cfl > 0.0)) return GAMER_E_PARAM;

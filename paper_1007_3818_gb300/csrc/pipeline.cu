@@ -20,6 +20,9 @@ extern "C" int gamer_hydro_advance_f32(const float*, float*, float*, const doubl
 extern "C" int gamer_hydro_advance_mixed(const float*, float*, float*, const double*,
                                          const double*, uint32_t*, double*, int64_t,
                                          const gh_params*, void*);
+extern "C" int gamer_hydro_advance_ff(const float*, float*, float*, const double*,
+                                         const double*, uint32_t*, double*, int64_t,
+                                         const gh_params*, void*);
 extern "C" int gamer_hydro_advance_f64(const double*, double*, double*, const double*,
                                        const double*, uint32_t*, double*, int64_t,
                                        const gh_params*, void*);
@@ -28,6 +31,11 @@ extern "C" int gamer_hydro_advance_level_window_f32(const float*, float*, float*
                                                     int32_t, const double*, const double*,
                                                     uint32_t*, double*, const gh_params*, void*);
 extern "C" int gamer_hydro_advance_level_window_mixed(const float*, float*, float*, int32_t,
+                                                      int32_t, int32_t, int32_t, int32_t, int32_t,
+                                                      int32_t, int32_t, const double*,
+                                                      const double*, uint32_t*, double*,
+                                                      const gh_params*, void*);
+extern "C" int gamer_hydro_advance_level_window_ff(const float*, float*, float*, int32_t,
                                                       int32_t, int32_t, int32_t, int32_t, int32_t,
                                                       int32_t, int32_t, const double*,
                                                       const double*, uint32_t*, double*,
@@ -142,7 +150,7 @@ extern "C" int gamer_pipeline_create(int32_t mode, int64_t batch_groups, int32_t
     using namespace gamer;
     if (!out) return GAMER_E_NULL;
     *out = nullptr;
-    if (mode < 0 || mode > 2 || batch_groups < 1 || batch_groups > (int64_t(1) << 24))
+    if (mode < 0 || mode > 3 || batch_groups < 1 || batch_groups > (int64_t(1) << 24))
         return GAMER_E_PARAM;
     const DeviceInfo d = current_device();
     if (d.status != GAMER_OK) return d.status;
@@ -236,6 +244,9 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
         else if (pl->mode == GAMER_MODE_MIXED)
             rc = gamer_hydro_advance_mixed((const float*)S.in, (float*)S.out, (float*)ff, S.dt,
                                            S.dh, S.status, S.partials, n, p, pl->s_comp);
+        else if (pl->mode == GAMER_MODE_FF)
+            rc = gamer_hydro_advance_ff((const float*)S.in, (float*)S.out, (float*)ff, S.dt,
+                                        S.dh, S.status, S.partials, n, p, pl->s_comp);
         else
             rc = gamer_hydro_advance_f64((const double*)S.in, (double*)S.out, (double*)ff, S.dt,
                                          S.dh, S.status, S.partials, n, p, pl->s_comp);
@@ -391,6 +402,11 @@ int level_step_resident(gamer_pipeline* pl, const char* hin, char* hout, int32_t
                 (const float*)din, (float*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
                 pl->lev_dt + g0, pl->lev_dt + G + g0, pl->lev_status + g0,
                 pl->lev_partials + g0 * 6, p, pl->s_comp);
+        else if (pl->mode == GAMER_MODE_FF)
+            rc = gamer_hydro_advance_level_window_ff(
+                (const float*)din, (float*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
+                pl->lev_dt + g0, pl->lev_dt + G + g0, pl->lev_status + g0,
+                pl->lev_partials + g0 * 6, p, pl->s_comp);
         else
             rc = gamer_hydro_advance_level_window_f64(
                 (const double*)din, (double*)o, nullptr, gx, gy, gz, bc, 0, gz, z0, nz,
@@ -518,6 +534,10 @@ extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* le
                 S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
         else if (pl->mode == GAMER_MODE_MIXED)
             rc = gamer_hydro_advance_level_window_mixed(
+                (const float*)S.win, (float*)S.wout, nullptr, gx, gy, gz, bc, zb, zn, z0, nz,
+                S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
+        else if (pl->mode == GAMER_MODE_FF)
+            rc = gamer_hydro_advance_level_window_ff(
                 (const float*)S.win, (float*)S.wout, nullptr, gx, gy, gz, bc, zb, zn, z0, nz,
                 S.wdt, S.wdt + n, S.wstatus, S.wpartials, p, pl->s_comp);
         else

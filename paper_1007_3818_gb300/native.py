@@ -15,7 +15,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgamer_gb300.so")
 
-GAMER_MODE_F32, GAMER_MODE_MIXED, GAMER_MODE_F64 = 0, 1, 2
+GAMER_MODE_F32, GAMER_MODE_MIXED, GAMER_MODE_F64, GAMER_MODE_FF = 0, 1, 2, 3
 ST_PREDICTOR_FALLBACK, ST_HLLE_FALLBACK, ST_NONPOSITIVE_OUT = 0x1, 0x2, 0x4
 ST_BAD_INPUT, ST_INTERNAL_TIMEOUT, ST_FLOOR = 0x8, 0x10, 0x20
 
@@ -60,17 +60,17 @@ def lib():
         vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         P = ctypes.POINTER
         for name in ("gamer_hydro_advance_f32", "gamer_hydro_advance_mixed",
-                     "gamer_hydro_advance_f64"):
+                     "gamer_hydro_advance_f64", "gamer_hydro_advance_ff"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(gh_params), vp]
             f.restype = ctypes.c_int
         for name in ("gamer_hydro_advance_level_f32", "gamer_hydro_advance_level_mixed",
-                     "gamer_hydro_advance_level_f64"):
+                     "gamer_hydro_advance_level_f64", "gamer_hydro_advance_level_ff"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, P(gh_params), vp]
             f.restype = ctypes.c_int
         for name in ("gamer_hydro_advance_level_window_f32", "gamer_hydro_advance_level_window_mixed",
-                     "gamer_hydro_advance_level_window_f64"):
+                     "gamer_hydro_advance_level_window_f64", "gamer_hydro_advance_level_window_ff"):
             f = getattr(L, name)
             f.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp,
                           P(gh_params), vp]
@@ -171,7 +171,7 @@ def _ptr(t, dtype=None, shape_tail=None, name="tensor"):
 
 
 _ADV = {GAMER_MODE_F32: "gamer_hydro_advance_f32", GAMER_MODE_MIXED: "gamer_hydro_advance_mixed",
-        GAMER_MODE_F64: "gamer_hydro_advance_f64"}
+        GAMER_MODE_F64: "gamer_hydro_advance_f64", GAMER_MODE_FF: "gamer_hydro_advance_ff"}
 
 
 def _advance(mode, inp, out, face_flux, dt, dh, status, partials, params, stream):
@@ -214,6 +214,7 @@ def hydro_advance(mode, inp, out, face_flux, dt, dh, status, partials, params, s
 
 _ADV_LEVEL = {GAMER_MODE_F32: "gamer_hydro_advance_level_f32",
               GAMER_MODE_MIXED: "gamer_hydro_advance_level_mixed",
+              GAMER_MODE_FF: "gamer_hydro_advance_level_ff",
               GAMER_MODE_F64: "gamer_hydro_advance_level_f64"}
 
 
@@ -256,6 +257,7 @@ def hydro_advance_level_window(mode, window, out, face_flux, gx, gy, gz, bc, zb,
             raise GamerError(-2, f"{nm} must hold gx*gy*nz = {N} groups")
     name = {GAMER_MODE_F32: "gamer_hydro_advance_level_window_f32",
             GAMER_MODE_MIXED: "gamer_hydro_advance_level_window_mixed",
+            GAMER_MODE_FF: "gamer_hydro_advance_level_window_ff",
             GAMER_MODE_F64: "gamer_hydro_advance_level_window_f64"}[mode]
     rc = getattr(lib(), name)(
         _ptr(window, T, (5, 16, 16, 16), "window"), _ptr(out, T, (5, 16, 16, 16), "out"),

@@ -20,7 +20,7 @@ import sys
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--path", choices=["tiles", "level", "both"], default="level")
-    ap.add_argument("--mode", choices=["f32", "mixed", "f64"], default="f32")
+    ap.add_argument("--mode", choices=["f32", "mixed", "f64", "ff"], default="f32")
     ap.add_argument("--groups", type=int, nargs=3, default=[16, 16, 8], metavar=("GX", "GY", "GZ"))
     ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM (0: the library default)")
     ap.add_argument("--variant", type=int, default=0)
@@ -32,7 +32,7 @@ def main(argv=None):
     from . import native, workloads as wl
 
     mode = {"f32": native.GAMER_MODE_F32, "mixed": native.GAMER_MODE_MIXED,
-            "f64": native.GAMER_MODE_F64}[a.mode]
+            "f64": native.GAMER_MODE_F64, "ff": native.GAMER_MODE_FF}[a.mode]
     T = torch.float64 if mode == native.GAMER_MODE_F64 else torch.float32
     gx, gy, gz = a.groups
     G = gx * gy * gz

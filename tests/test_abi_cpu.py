@@ -67,7 +67,7 @@ def _adv(lib, name, in_=FAKE, out=FAKE + (1 << 30), ff=None, dt=FAKE + (2 << 30)
 
 
 @pytest.mark.parametrize("name", ["gamer_hydro_advance_f32", "gamer_hydro_advance_mixed",
-                                  "gamer_hydro_advance_f64"])
+                                  "gamer_hydro_advance_f64", "gamer_hydro_advance_ff"])
 def test_advance_rejects_bad_arguments(lib, name):
     assert _adv(lib, name, N=-1) == -2
     assert _adv(lib, name, N=0) == 0  # no-op, returns before touching the device
@@ -97,7 +97,8 @@ def test_advance_rejects_bad_arguments(lib, name):
 
 @pytest.mark.parametrize("name", ["gamer_hydro_advance_level_f32",
                                   "gamer_hydro_advance_level_mixed",
-                                  "gamer_hydro_advance_level_f64"])
+                                  "gamer_hydro_advance_level_f64",
+                                  "gamer_hydro_advance_level_ff"])
 def test_advance_level_rejects_bad_arguments(lib, name):
     f = getattr(lib, name)
     prm = native.make_params(1.4)
@@ -195,9 +196,10 @@ def test_hydro_dt_rejects_bad_arguments(lib):
 
 
 def test_set_launch_shape_validation(lib):
-    assert lib.gamer_set_hydro_ctas_per_sm(3, 1) == -2
+    assert lib.gamer_set_hydro_ctas_per_sm(4, 1) == -2
     assert lib.gamer_set_hydro_ctas_per_sm(0, -1) == -2
     assert lib.gamer_set_hydro_ctas_per_sm(0, 0) == 0
+    assert lib.gamer_set_hydro_ctas_per_sm(3, 0) == 0                # the float-float mode
 
 
 def test_binding_fails_loudly_without_library(monkeypatch):
