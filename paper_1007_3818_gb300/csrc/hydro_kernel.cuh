@@ -94,6 +94,7 @@ struct KConst {
     int floors;         // bit 0: density floor on, bit 1: pressure floor on
     T rho_floor, p_floor;
     P eth_floor;        // p_floor / (gamma - 1)
+    T gm1_lo;           // gamma - 1 - gm1: the float-float mode's low part
 };
 
 // row slot of a 16-wide face / flux array (see the bank note above)
@@ -132,7 +133,11 @@ __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KC
         const float kh = 0.5f * p, kl = 0.5f * (pe + fmaf(s, il, se * ir));
         float de;
         const float d = two_sum(E, -kh, de);
-        return kc.gm1 * (d + (de - kl));
+        const float dl = de - kl;
+        // (gm1 + gm1_lo) (d + dl), rounded once
+        const float ph = kc.gm1 * d;
+        const float pl = fmaf(kc.gm1, d, -ph) + fmaf(kc.gm1, dl, kc.gm1_lo * d);
+        return ph + pl;
     } else {
         return kc.gm1 * (E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
     }

@@ -54,6 +54,7 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     KConst<T, P> kc;
     kc.gamma = T(p->gamma);
     kc.gm1 = T(p->gamma - 1.0);
+    kc.gm1_lo = T((p->gamma - 1.0) - double(kc.gm1));
     kc.gm1p = P(p->gamma - 1.0);
     kc.limiter = p->limiter;
     kc.pfb = p->predictor_fallback;

@@ -54,7 +54,7 @@ def run(problem, n, steps, cores, rho_floor=0.0, p_floor=0.0, cfl=0.5):
     t_oracle = time.perf_counter() - t0
     out = {"problem": problem, "n": n, "steps": steps, "t_end": float(sum(dts)),
            "oracle_s": t_oracle, "floors": fl, "cfl": cfl, "oracle_status_or": ref_status}
-    for mode, name in ((0, "f32"), (1, "mixed"), (2, "f64")):
+    for mode, name in ((0, "f32"), (1, "mixed"), (3, "ff"), (2, "f64")):
         T = torch.float64 if mode == 2 else torch.float32
         cur = torch.from_numpy(G).to("cuda", T)
         nxt = torch.empty_like(cur)
