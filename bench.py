@@ -278,7 +278,9 @@ def streamed_main(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         dt = CFL * dh / float(part[:, 0].max())          # FP64 reduction of the partials
+        torch.cuda.nvtx.range_push("streamed level step")
         pl.level_step_host(lv[cur], lv[1 - cur], gx, gx, gx, 0, dt, dh, st, part, params)
+        torch.cuda.nvtx.range_pop()
         cur = 1 - cur
     el = time.perf_counter() - t0
     clk = clocks.stop()
@@ -368,6 +370,7 @@ def main():
         # FP64 dt / conservation reduction that feeds the next step's dt
         nonlocal nxt
         src, dst = cur[nxt], cur[1 - nxt]
+        torch.cuda.nvtx.range_push("level step")
         if i is not None:
             ev_a[i].record(stream)
         native.hydro_advance_level(mode, src, dst, ff, gx, gy, gz, 0, dt_g, dh_g, status,
@@ -375,6 +378,7 @@ def main():
         if i is not None:
             ev_b[i].record(stream)
         native.gamer_hydro_dt(partials, None, dh_level, CFL, dt_level, totals, dt_g, ws)
+        torch.cuda.nvtx.range_pop()
         nxt = 1 - nxt
 
     for _ in range(args.warmup):

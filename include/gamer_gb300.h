@@ -393,6 +393,15 @@ int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
  * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide setting. */
 int gamer_set_hydro_variant(int32_t variant);
 
+/* Debug facility (not part of the scheme): with on = 1, every later launch of
+ * the level kernels (gamer_hydro_advance_level_*, _level_window_*) fills each
+ * shared-memory input slot with NaN before gathering a plane into it (one
+ * extra CTA barrier per plane), so a stencil read of a cell the gather does
+ * not copy turns the results into NaN.  Results are unchanged when the gather
+ * covers every cell read.  Process-wide; 0 (default) turns it off.  Returns
+ * GAMER_E_PARAM for other values. */
+int gamer_set_debug_poison(int32_t on);
+
 /*
  * AMR coarse-fine coupling after one coarse step and its fine sub-steps: the
  * step that consumes the face fluxes of gamer_hydro_advance_*.  The paper

@@ -34,6 +34,11 @@ DeviceInfo current_device() {
     return d;
 }
 
+int& hydro_debug_poison() {
+    static int v = 0;
+    return v;
+}
+
 int& hydro_variant() {
     static int v = 0;
     return v;
@@ -76,5 +81,11 @@ extern "C" int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm) {
 extern "C" int gamer_set_hydro_variant(int32_t variant) {
     if (variant < 0 || variant > 2) return GAMER_E_PARAM;
     gamer::hydro_variant() = variant;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_set_debug_poison(int32_t on) {
+    if (on != 0 && on != 1) return GAMER_E_PARAM;
+    gamer::hydro_debug_poison() = on;
     return GAMER_OK;
 }

@@ -772,6 +772,7 @@ __device__ __forceinline__ void issue_plane(SM& S, const T* gin, int kp) {
 struct LevelGeom {
     int gx, gy, gz, bc;
     int zb, z0;
+    int poison;  // debug: fill each input slot with NaN before gathering into it
 };
 
 // Level coordinate X, at most two cells outside [0, n), mapped into the level:
@@ -928,6 +929,15 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
         *plan = make_plan<T>(geo, bx, by);  // read back by this thread only
     }
     template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {
+        if (L.poison) {
+            // debug: cells the gather does not write read back as NaN, so a
+            // stencil read outside the gathered set shows up in the results
+            // (the slot's previous plane was consumed before this call)
+            T* slot = S.raw[(kp + 2) % RING];
+            for (int c = threadIdx.x; c < 5 * kPlane + 4; c += kThreads)
+                slot[c] = __int_as_float(0x7fc00000) + T(0);
+            __syncthreads();
+        }
         const GatherPlan P = *plan;
         gather_plane<RING>(S, level, L, P, bz, kp);
     }

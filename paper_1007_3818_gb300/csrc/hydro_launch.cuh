@@ -12,6 +12,7 @@ int& hydro_ctas_per_sm_override(int mode);
 // Code-shape variant of the FP32 kernel (0: inline Riemann solver, 1: one
 // out-of-line copy); chosen by the autotuner.
 int& hydro_variant();
+int& hydro_debug_poison();
 
 // Common launch path.  SRC 0: `in` = N tiles [N][5][20]^3; SRC 1: `in` = the
 // level `geo` (N = gx*gy*gz), ghosts gathered in the kernel.
@@ -153,7 +154,7 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                   typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
                   uint32_t* status, double* partials, int64_t N, const gh_params* p,
                   void* stream) {
-    const LevelGeom geo = {1, 1, 1, 0, 0, 0};
+    const LevelGeom geo = {1, 1, 1, 0, 0, 0, 0};
     return hydro_launch<MODE, 0>(in, out, face_flux, dt, dh, status, partials, N, p, geo,
                                  stream);
 }
@@ -170,7 +171,7 @@ int hydro_advance_level(const typename Prec<MODE>::T* level, typename Prec<MODE>
     // the gather's per-group plan holds level offsets within a z-layer of
     // groups in units of 16 cells as 32-bit integers
     if (int64_t(gx) * gy * 1280 + 2048 > INT32_MAX) return GAMER_E_PARAM;
-    const LevelGeom geo = {gx, gy, gz, bc, 0, 0};
+    const LevelGeom geo = {gx, gy, gz, bc, 0, 0, hydro_debug_poison()};
     return hydro_launch<MODE, 1>(level, out, face_flux, dt, dh, status, partials,
                                  int64_t(gx) * gy * gz, p, geo, stream, gz);
 }
@@ -201,7 +202,7 @@ int hydro_advance_level_window(const typename Prec<MODE>::T* window, typename Pr
         }
         if ((zz - zb + gz) % gz >= zn) return GAMER_E_PARAM;
     }
-    const LevelGeom geo = {gx, gy, gz, bc, zb, z0};
+    const LevelGeom geo = {gx, gy, gz, bc, zb, z0, hydro_debug_poison()};
     return hydro_launch<MODE, 1>(window, out, face_flux, dt, dh, status, partials,
                                  int64_t(gx) * gy * nz, p, geo, stream, zn);
 }

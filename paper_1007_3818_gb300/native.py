@@ -102,6 +102,8 @@ def lib():
         L.gamer_version.restype = ctypes.c_char_p
         L.gamer_set_hydro_variant.argtypes = [i32]
         L.gamer_set_hydro_variant.restype = ctypes.c_int
+        L.gamer_set_debug_poison.argtypes = [i32]
+        L.gamer_set_debug_poison.restype = ctypes.c_int
         L.gamer_set_hydro_ctas_per_sm.argtypes = [i32, i32]
         L.gamer_set_hydro_ctas_per_sm.restype = ctypes.c_int
         L.gamer_microbench.argtypes = [i32, i64, vp, i64, P(d), vp]
@@ -422,6 +424,11 @@ def gamer_version():
 def gamer_set_hydro_ctas_per_sm(mode, ctas_per_sm):
     _check(lib().gamer_set_hydro_ctas_per_sm(int(mode), int(ctas_per_sm)),
            "gamer_set_hydro_ctas_per_sm")
+
+
+def gamer_set_debug_poison(on):
+    """Debug: NaN-fill the level kernels' input slots before each gather."""
+    _check(lib().gamer_set_debug_poison(int(on)), "gamer_set_debug_poison")
 
 
 def gamer_set_hydro_variant(variant):

@@ -589,6 +589,48 @@ def test_level_window_equals_full_level(mode, bc):
         assert torch.equal(st, st_full[sl]) and torch.equal(part, part_full[sl])
 
 
+@pytest.fixture
+def poison_guard():
+    from paper_1007_3818_gb300 import native
+    native.gamer_set_debug_poison(1)
+    yield native
+    native.gamer_set_debug_poison(0)
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED, F64, FF], ids=["f32", "mixed", "f64", "ff"])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1)])
+def test_fused_level_with_poisoned_slots(poison_guard, mode, bc, dims):
+    """Debug poison: every input slot NaN-filled before each gather.  The
+    gather copies only the cells the stencil reads (R10), so the results, the
+    status and the partials stay bit for bit those of ghost fill + tile step."""
+    _fused_vs_fill(mode, bc, dims)
+
+
+def test_level_window_with_poisoned_slots(poison_guard):
+    import torch
+    native = poison_guard
+    g = 5 / 3
+    gx, gy, gz = 2, 3, 4
+    layer, G = gx * gy, gx * gy * gz
+    lv = np.concatenate([wl.level_to_groups(wl.fourier_level(n=16, seed=200 + i, gamma=g))
+                         for i in range(G)])
+    d_lv = torch.from_numpy(lv).to("cuda", torch.float32)
+    p = native.make_params(g)
+    full = torch.empty_like(d_lv)
+    vec = lambda v, n: torch.full((n,), v, device="cuda", dtype=torch.float64)  # noqa: E731
+    native.gamer_set_debug_poison(0)
+    native.hydro_advance_level(F32, d_lv, full, None, gx, gy, gz, 0, vec(2e-3, G), vec(1 / 64, G),
+                               None, None, p)
+    native.gamer_set_debug_poison(1)
+    win = torch.cat([d_lv[z * layer:(z + 1) * layer] for z in (3, 0, 1)]).contiguous()
+    out = torch.empty((layer, 5, 16, 16, 16), device="cuda")
+    native.hydro_advance_level_window(F32, win, out, None, gx, gy, gz, 0, 3, 0, 1,
+                                      vec(2e-3, layer), vec(1 / 64, layer), None, None, p)
+    torch.cuda.synchronize()
+    assert torch.equal(out, full[:layer])
+
+
 def test_fused_level_rejects_in_place_update():
     import torch
     from paper_1007_3818_gb300 import native
