@@ -1074,8 +1074,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (__syncthreads_or(timed_out)) goto abort_group;
 
         {
-            // owner registers: z+ state of the previous plane, previous z-flux,
-            // U - lam * (x/y flux divergence) of the previous plane
+            // owner registers: z+ state of the previous plane, the flux of the
+            // z face below it, and E = U - lam (x/y flux divergence) of it
             T zp0[5], zp1[5], fzo0[5], fzo1[5], E0[5], E1[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q)
@@ -1083,53 +1083,44 @@ __global__ void __launch_bounds__(kThreads, MINB)
             T smax = T(0);
             SumAcc<T> sums;
 
-            // Per plane k, two barriers: phase CA runs C(k-1) -- finish plane
-            // k-2 and set up plane k-1 from the fluxes of phase B(k-1) -- then
+            // Per plane k, two barriers: phase CA runs C(k-1) -- the x/y flux
+            // divergence of plane k-1 from the fluxes of phase B(k-1) -- then
             // A(k), the half-step prediction of plane k; phase B(k) solves the
-            // Riemann problems of plane k and converts plane k+2.  C only reads
-            // what B wrote and A only writes what B reads next, so C(k-1) and
-            // A(k) share a phase.
-            T zm0[5], zm1[5], zpn0[5], zpn1[5], uc0[5], uc1[5], fz0[5], fz1[5];
+            // z faces k-1/2, which completes plane k-1 (written out at once),
+            // then the x/y faces of plane k, and converts plane k+2.  C only
+            // reads what B wrote and A only writes what B reads next, so C(k-1)
+            // and A(k) share a phase.  Across the x/y solves only U, the lower
+            // z flux and the z+ state of plane k stay in registers.  The two z
+            // fluxes of a cell are differenced before scaling, so equal fluxes
+            // cancel exactly (a uniform state stays bitwise uniform).
+            T zm0[5], zm1[5], zpn0[5], zpn1[5], uc0[5], uc1[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
-                zm0[q] = zm1[q] = zpn0[q] = zpn1[q] = uc0[q] = uc1[q] = fz0[q] = fz1[q] = T(0);
-            for (int k = -1; k <= 17; ++k) {
+            for (int q = 0; q < 5; ++q) zm0[q] = zm1[q] = zpn0[q] = zpn1[q] = uc0[q] = uc1[q] = T(0);
+            // plane kk of column (jj, i0) from its final conserved state o:
+            // floors, output, positivity flag, signal speed and sums
+            auto finish = [&](T o[5], int kk, int jj) {
+                T ir = rcp_(o[0]);
+                T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
+                if (kc.floors) apply_floors<MODE>(o, ir, p, kc, st);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
+                if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
+                const T c2 = kc.gamma * p * ir;
+                const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
+                const T sp = max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
+                if (sp > smax) smax = sp;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
+            };
+            for (int k = -1; k <= 16; ++k) {
                 const T* Wm = S.W[(k + 1) % 3];
                 const T* W0 = S.W[(k + 2) % 3];
                 const T* Wp = S.W[(k + 3) % 3];
                 const T* Uk = S.raw[(k + 2) % RING] + ROFF;
                 const bool inner = (k >= 0 && k <= 15);
 
-                // ---- phase CA, part C(k-1): finish plane k-2, set up plane k-1
-                if (k - 1 >= 1) {
-                    const int kk = k - 2;
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        if (cc == 1 && !two) break;
-                        const T* Ep = cc ? E1 : E0;
-                        const T* fo = cc ? fzo1 : fzo0;
-                        const T* fn = cc ? fz1 : fz0;
-                        const int jj = cc ? j1 : j0;
-                        T o[5];
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) o[q] = Ep[q] - lam * (fn[q] - fo[q]);
-                        // epilogue: floors, positivity flag, signal speed and sums
-                        T ir = rcp_(o[0]);
-                        T p = pressure<MODE>(o[0], o[1], o[2], o[3], o[4], ir, kc);
-                        if (kc.floors) apply_floors<MODE>(o, ir, p, kc, st);
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
-                        if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
-                        const T c2 = kc.gamma * p * ir;
-                        const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
-                        const T sp =
-                            max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
-                        if (sp > smax) smax = sp;
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
-                    }
-                }
-                if (k - 1 >= 0 && k - 1 <= 15) {
+                // ---- phase CA, part C(k-1): x/y divergence of plane k-1
+                if (k - 1 >= 0) {
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (cc == 1 && !two) break;
@@ -1139,14 +1130,11 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         const int ryp = 272 + ((jj == 15) ? (256 + i0) : (frow(jj + 1) * 16 + i0));
                         const T* uc = cc ? uc1 : uc0;
                         T* Ec = cc ? E1 : E0;
-                        T* fo = cc ? fzo1 : fzo0;
-                        const T* fn = cc ? fz1 : fz0;
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
                             const T* fq = S.fxy + q * kFluxStride;
                             const T D = (fq[rxp] - fq[fa]) + (fq[ryp] - fq[272 + fa]);
                             Ec[q] = uc[q] - lam * D;
-                            fo[q] = fn[q];
                         }
                     }
                 }
@@ -1155,7 +1143,6 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     zp0[q] = zpn0[q];
                     zp1[q] = zpn1[q];
                 }
-                if (k == 17) break;  // plane 15 is finished; nothing left to predict
 
                 // ---- phase CA, part A(k): half-step prediction of plane k
                 {
@@ -1209,32 +1196,36 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
                 // ---- phase B(k): Riemann solves
                 if (k >= 0) {
-                    // z faces k-1/2 of the owned columns: rotated (rho, m_z, m_x, m_y, E)
-                    {
-                        T L[5] = {zp0[0], zp0[3], zp0[1], zp0[2], zp0[4]};
-                        T R[5] = {zm0[0], zm0[3], zm0[1], zm0[2], zm0[4]};
+                    // z faces k-1/2 of the owned columns, rotated (rho, m_z, m_x,
+                    // m_y, E): the flux leaves plane k-1, which is then final,
+                    // and enters plane k
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cc == 1 && !two) break;
+                        const T* zp = cc ? zp1 : zp0;
+                        const T* zm = cc ? zm1 : zm0;
+                        const int jj = cc ? j1 : j0;
+                        T L[5] = {zp[0], zp[3], zp[1], zp[2], zp[4]};
+                        T R[5] = {zm[0], zm[3], zm[1], zm[2], zm[4]};
                         T F[5];
                         roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
-                        fz0[0] = F[0]; fz0[3] = F[1]; fz0[1] = F[2]; fz0[2] = F[3]; fz0[4] = F[4];
+                        const T fz[5] = {F[0], F[2], F[3], F[1], F[4]};
                         const int pz = flux_plane(2, k, kc.flux9);
                         if (gff && pz >= 0) {
-                            T* dst = gff + pz * kFluxPlane + j0 * 16 + i0;
+                            T* dst = gff + pz * kFluxPlane + jj * 16 + i0;
 #pragma unroll
-                            for (int q = 0; q < 5; ++q) dst[q * 256] = fz0[q];
+                            for (int q = 0; q < 5; ++q) dst[q * 256] = fz[q];
                         }
-                    }
-                    if (two) {
-                        T L[5] = {zp1[0], zp1[3], zp1[1], zp1[2], zp1[4]};
-                        T R[5] = {zm1[0], zm1[3], zm1[1], zm1[2], zm1[4]};
-                        T F[5];
-                        roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
-                        fz1[0] = F[0]; fz1[3] = F[1]; fz1[1] = F[2]; fz1[2] = F[3]; fz1[4] = F[4];
-                        const int pz = flux_plane(2, k, kc.flux9);
-                        if (gff && pz >= 0) {
-                            T* dst = gff + pz * kFluxPlane + j1 * 16 + i0;
+                        T* fo = cc ? fzo1 : fzo0;
+                        if (k >= 1) {
+                            const T* Ec = cc ? E1 : E0;
+                            T o[5];
 #pragma unroll
-                            for (int q = 0; q < 5; ++q) dst[q * 256] = fz1[q];
+                            for (int q = 0; q < 5; ++q) o[q] = Ec[q] - lam * (fz[q] - fo[q]);
+                            finish(o, k - 1, jj);
                         }
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) fo[q] = fz[q];
                     }
                 }
                 if (inner) {
