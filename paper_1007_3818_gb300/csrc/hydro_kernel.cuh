@@ -240,7 +240,7 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
     const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
     T FL[5], FR[5];
     {
-        const T mL = L[0] * uL, mR = R[0] * uR;
+        const T mL = L[1], mR = R[1];  // rho u_n is the normal momentum itself
         FL[0] = mL;
         FL[1] = mL * uL + pL;
         FL[2] = mL * vL;
@@ -305,10 +305,11 @@ __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst
     const T d5 = max_(T(0), max_(K5u - l5s, (uR + cR) - K5u));
     if (e5 < d5) e5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
     const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
+    // sum over waves of s_i K_i; K1, K2, K5 share the transverse velocities
     const T D0 = s1 + s2 + s5;
     const T D1 = s1 * K1u + s2 * uT + s5 * K5u;
-    const T D2 = s1 * vT + s2 * vT + s3 + s5 * vT;
-    const T D3 = s1 * wT + s2 * wT + s4 + s5 * wT;
+    const T D2 = D0 * vT + s3;
+    const T D3 = D0 * wT + s4;
     const T D4 = s1 * K1E + s2 * (T(0.5) * q2) + s3 * vT + s4 * wT + s5 * K5E;
     F[0] = T(0.5) * (FL[0] + FR[0]) - T(0.5) * D0;
     F[1] = T(0.5) * (FL[1] + FR[1]) - T(0.5) * D1;
@@ -329,7 +330,7 @@ __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KCons
     const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
     const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
     const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
-    const T mL = L[0] * uL, mR = R[0] * uR;
+    const T mL = L[1], mR = R[1];
     const T cL = sqrt_(kc.gamma * pL * irL);
     const T cR = sqrt_(kc.gamma * pR * irR);
     const T HL = (L[4] + pL) * irL;
@@ -374,8 +375,8 @@ __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KCons
     const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
     const T D0 = s1 + s2 + s5;
     const T D1 = s1 * K1u + s2 * uT + s5 * K5u;
-    const T D2 = s1 * vT + s2 * vT + s3 + s5 * vT;
-    const T D3 = s1 * wT + s2 * wT + s4 + s5 * wT;
+    const T D2 = D0 * vT + s3;
+    const T D3 = D0 * wT + s4;
     const T D4 = s1 * K1E + s2 * (T(0.5) * q2) + s3 * vT + s4 * wT + s5 * K5E;
     F[0] = T(0.5) * (mL + mR) - T(0.5) * D0;
     F[1] = T(0.5) * ((mL * uL + pL) + (mR * uR + pR)) - T(0.5) * D1;
@@ -403,7 +404,7 @@ __device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P
     const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
     const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
     T FL[5], FR[5];
-    const T mL = L[0] * uL, mR = R[0] * uR;
+    const T mL = L[1], mR = R[1];
     FL[0] = mL; FL[1] = mL * uL + pL; FL[2] = mL * vL; FL[3] = mL * wL; FL[4] = (L[4] + pL) * uL;
     FR[0] = mR; FR[1] = mR * uR + pR; FR[2] = mR * vR; FR[3] = mR * wR; FR[4] = (R[4] + pR) * uR;
     const T cL = sqrt_(kc.gamma * pL * irL);
@@ -503,7 +504,8 @@ __device__ __forceinline__ void hllc_rot(const T L[5], const T R[5], const KCons
 
 // Riemann solve by variant: 0 Roe inline, 1 Roe through one out-of-line
 // copy, 2 HLLC inline.  (The kernel's RSV template argument carries this in
-// bits 0-1 and the reconstruction, 0 primitive / 1 characteristic, in bit 2.)
+// bits 0-1, the reconstruction, 0 primitive / 1 characteristic, in bit 2 and
+// a compiled-in van Leer limiter in bit 3.)
 template <int RSV> struct RoeTag {};
 template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_pick(RoeTag<0>, const T L[5], const T R[5],
@@ -971,7 +973,8 @@ template <> struct SumAcc<float> {
 // TMA engine; SRC 1: `in` is the uniform level `geo` (N = gx*gy*gz groups) and
 // each plane is gathered from the group and its neighbours (fused ghost fill).
 // RSV: bits 0-1 the Riemann solver (0 Roe inline, 1 Roe out of line, 2 HLLC),
-// bit 2 characteristic (1) or primitive (0) slope limiting.
+// bit 2 characteristic (1) or primitive (0) slope limiting, bit 3 the van Leer
+// limiter compiled in (1) or the limiter read from kc.limiter per slope (0).
 // RING: input planes in flight (2: the copy of plane k+2 goes out after phase A
 // of plane k; 3: plane k+3 does, one full iteration ahead of its use).
 template <int MODE, int MINB, int RSV = 0, int SRC = 0, int RING = 2>
@@ -984,6 +987,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
                       KConst<typename Prec<MODE>::T, typename Prec<MODE>::P> kc,
                       LevelGeom geo) {
     using T = typename Prec<MODE>::T;
+    constexpr int kLim = (RSV & 8) ? 0 : -1;  // van Leer compiled in, or kc.limiter
+    constexpr int kRec = (RSV >> 2) & 1;
     extern __shared__ __align__(128) unsigned char smem_bytes[];
     Smem<T, RING>& S = *reinterpret_cast<Smem<T, RING>*>(smem_bytes);
     constexpr int ROFF = raw_offset<SRC, T>();
@@ -1149,7 +1154,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
                     T fs[6][5];
-                    predict<MODE, -1, (RSV >> 2)>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs,
+                    predict<MODE, kLim, kRec>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs,
                                                   st);
                     if (inner) {
 #pragma unroll
@@ -1170,7 +1175,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc_b];
                     T fs[6][5];
-                    predict<MODE, -1, (RSV >> 2)>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs,
+                    predict<MODE, kLim, kRec>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs,
                                                   st);
                     if (inner) {
 #pragma unroll

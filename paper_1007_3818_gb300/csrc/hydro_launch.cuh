@@ -106,15 +106,20 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     // (the fused gather adds its per-thread plans after the Smem block)
     constexpr int extra = int(PlaneLoader<SRC, 2, T>::kExtraSmem);
     int smem = int(sizeof(Smem<T, 2>)) + extra;
+    // the default limiter (van Leer) is compiled into the default builds;
+    // the others are read per slope from kc.limiter
+    const bool vl = p->limiter == 0;
     if constexpr (MODE == GAMER_MODE_F64) {
-        kern = hydro_step_kernel<MODE, 1, 0, SRC, 3>;
+        kern = vl ? hydro_step_kernel<MODE, 1, 8, SRC, 3> : hydro_step_kernel<MODE, 1, 0, SRC, 3>;
         smem = int(sizeof(Smem<T, 3>)) + extra;
     } else {
         if (want == 2) {
-            kern = hydro_step_kernel<MODE, 2, 0, SRC, 3>;
+            kern = vl ? hydro_step_kernel<MODE, 2, 8, SRC, 3>
+                      : hydro_step_kernel<MODE, 2, 0, SRC, 3>;
             smem = int(sizeof(Smem<T, 3>)) + extra;
         } else {
-            kern = hydro_step_kernel<MODE, 3, 0, SRC, 2>;
+            kern = vl ? hydro_step_kernel<MODE, 3, 8, SRC, 2>
+                      : hydro_step_kernel<MODE, 3, 0, SRC, 2>;
         }
         if constexpr (MODE == GAMER_MODE_F32 && SRC == 0) {
             if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
