@@ -228,100 +228,12 @@ __device__ __forceinline__ void hlle_rot(const T L[5], const T R[5], const T FL[
 }
 
 // Roe flux through a face whose normal is the first velocity component of the
-// rotated states L, R = (rho, m_n, m_t1, m_t2, E).  Sets GAMER_ST_HLLE_FALLBACK
-// in st when the HLLE fallback is used.
-template <int MODE, class T, class P>
-__device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
-                                        T F[5], uint32_t& st) {
-    const T irL = rcp_(L[0]), irR = rcp_(R[0]);
-    const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
-    const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
-    const T pL = pressure<MODE>(L[0], L[1], L[2], L[3], L[4], irL, kc);
-    const T pR = pressure<MODE>(R[0], R[1], R[2], R[3], R[4], irR, kc);
-    T FL[5], FR[5];
-    {
-        const T mL = L[1], mR = R[1];  // rho u_n is the normal momentum itself
-        FL[0] = mL;
-        FL[1] = mL * uL + pL;
-        FL[2] = mL * vL;
-        FL[3] = mL * wL;
-        FL[4] = (L[4] + pL) * uL;
-        FR[0] = mR;
-        FR[1] = mR * uR + pR;
-        FR[2] = mR * vR;
-        FR[3] = mR * wR;
-        FR[4] = (R[4] + pR) * uR;
-    }
-    const T cL = sqrt_(kc.gamma * pL * irL);
-    const T cR = sqrt_(kc.gamma * pR * irR);
-    const T HL = (L[4] + pL) * irL;
-    const T HR = (R[4] + pR) * irR;
-    const T rr = sqrt_(R[0] * irL);
-    const T i1 = rcp_(T(1) + rr);
-    const T uT = (uL + rr * uR) * i1;
-    const T vT = (vL + rr * vR) * i1;
-    const T wT = (wL + rr * wR) * i1;
-    const T HT = (HL + rr * HR) * i1;
-    const T q2 = uT * uT + vT * vT + wT * wT;
-    const T cT2 = kc.gm1 * (HT - T(0.5) * q2);
-    if (!(cT2 > T(0))) {
-        // no Roe sound speed: Davis's bounds over both states (S_L < S_R)
-        st |= GAMER_ST_HLLE_FALLBACK;
-        hlle_rot(L, R, FL, FR, min_(uL - cL, uR - cR), max_(uR + cR, uL + cL), F);
-        return;
-    }
-    const T cT = sqrt_(cT2);
-    const T rT = rr * L[0];
-    const T dr = R[0] - L[0], du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
-    const T ic2 = rcp_(cT2);
-    const T a1 = (dp - rT * cT * du) * (T(0.5) * ic2);
-    const T a2 = dr - dp * ic2;
-    const T a3 = rT * dv;
-    const T a4 = rT * dw;
-    const T a5 = (dp + rT * cT * du) * (T(0.5) * ic2);
-    const T K1u = uT - cT, K5u = uT + cT;
-    const T K1E = HT - uT * cT, K5E = HT + uT * cT;
-    // Roe intermediate states U*_L = U_L + a1 K1, U*_R = U_R - a5 K5
-    const T s1r = L[0] + a1, s1n = L[1] + a1 * K1u, s1a = L[2] + a1 * vT, s1b = L[3] + a1 * wT,
-            s1E = L[4] + a1 * K1E;
-    const T s4r = R[0] - a5, s4n = R[1] - a5 * K5u, s4a = R[2] - a5 * vT, s4b = R[3] - a5 * wT,
-            s4E = R[4] - a5 * K5E;
-    const T is1 = rcp_(s1r), is4 = rcp_(s4r);
-    const T p1 = pressure<MODE>(s1r, s1n, s1a, s1b, s1E, is1, kc);
-    const T p4 = pressure<MODE>(s4r, s4n, s4a, s4b, s4E, is4, kc);
-    if (!(s1r > T(0) && p1 > T(0) && s4r > T(0) && p4 > T(0))) {
-        st |= GAMER_ST_HLLE_FALLBACK;
-        hlle_rot(L, R, FL, FR, min_(uL - cL, K1u), max_(uR + cR, K5u), F);
-        return;
-    }
-    // Harten's smoothing with Harten-Hyman widths from the states beside
-    // each acoustic wave.
-    const T l1s = s1n * is1 - sqrt_(kc.gamma * p1 * is1);
-    const T l5s = s4n * is4 + sqrt_(kc.gamma * p4 * is4);
-    T e1 = abs_(K1u), e5 = abs_(K5u);
-    const T e2 = abs_(uT);
-    const T d1 = max_(T(0), max_(K1u - (uL - cL), l1s - K1u));
-    if (e1 < d1) e1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
-    const T d5 = max_(T(0), max_(K5u - l5s, (uR + cR) - K5u));
-    if (e5 < d5) e5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
-    const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
-    // sum over waves of s_i K_i; K1, K2, K5 share the transverse velocities
-    const T D0 = s1 + s2 + s5;
-    const T D1 = s1 * K1u + s2 * uT + s5 * K5u;
-    const T D2 = D0 * vT + s3;
-    const T D3 = D0 * wT + s4;
-    const T D4 = s1 * K1E + s2 * (T(0.5) * q2) + s3 * vT + s4 * wT + s5 * K5E;
-    F[0] = T(0.5) * (FL[0] + FR[0]) - T(0.5) * D0;
-    F[1] = T(0.5) * (FL[1] + FR[1]) - T(0.5) * D1;
-    F[2] = T(0.5) * (FL[2] + FR[2]) - T(0.5) * D2;
-    F[3] = T(0.5) * (FL[3] + FR[3]) - T(0.5) * D3;
-    F[4] = T(0.5) * (FL[4] + FR[4]) - T(0.5) * D4;
-}
-
-// Branch-free Roe flux (rotated frame, as roe_rot) without the fallback:
-// returns true when the HLLE fallback must replace F (Roe sound speed squared
-// not positive, or an intermediate state with rho <= 0 or p <= 0).  Having no
-// branch, two calls in a row are scheduled as one block of independent work.
+// rotated states L, R = (rho, m_n, m_t1, m_t2, E), with Harten's smoothing of
+// the acoustic eigenvalues and Harten-Hyman widths from the states beside each
+// acoustic wave.  Branch-free: returns true when the HLLE fallback must
+// replace F (Roe sound speed squared not positive, or an intermediate state
+// with rho <= 0 or p <= 0; F is then meaningless).  Having no branch, the
+// whole solve is one block of instructions the scheduler can interleave.
 template <int MODE, class T, class P>
 __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KConst<T, P>& kc,
                                          T F[5]) {
@@ -395,9 +307,8 @@ struct RoeIO {
     uint32_t st;
 };
 template <int MODE, class T, class P>
-__device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P> kc) {
-    const T* L = Li.v;
-    const T* R = Ri.v;
+__device__ __forceinline__ void hlle_core(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                          T F[5]) {
     const T irL = rcp_(L[0]), irR = rcp_(R[0]);
     const T uL = L[1] * irL, vL = L[2] * irL, wL = L[3] * irL;
     const T uR = R[1] * irR, vR = R[2] * irR, wR = R[3] * irR;
@@ -423,8 +334,12 @@ __device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P
         sl = min_(sl, uR - cR);
         sr = max_(sr, uL + cL);
     }
+    hlle_rot(L, R, FL, FR, sl, sr, F);
+}
+template <int MODE, class T, class P>
+__device__ __noinline__ RoeIO<T> hlle_full(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P> kc) {
     RoeIO<T> out;
-    hlle_rot(L, R, FL, FR, sl, sr, out.v);
+    hlle_core<MODE>(Li.v, Ri.v, kc, out.v);
     out.st = GAMER_ST_HLLE_FALLBACK;
     return out;
 }
@@ -443,6 +358,16 @@ __device__ __forceinline__ void hlle_apply(const T L[5], const T R[5], const KCo
 #pragma unroll
     for (int q = 0; q < 5; ++q) F[q] = r.v[q];
     st |= r.st;
+}
+
+// Roe flux with its HLLE fallback (sets GAMER_ST_HLLE_FALLBACK in st when
+// used): the branch-free solve, then one rarely taken branch into the single
+// out-of-line HLLE copy (measured faster than an inline fallback per call
+// site, which adds spills).
+template <int MODE, class T, class P>
+__device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
+                                        T F[5], uint32_t& st) {
+    if (roe_main<MODE>(L, R, kc, F)) hlle_apply<MODE>(L, R, kc, F, st);
 }
 
 // Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
