@@ -184,15 +184,15 @@ template <int MODE, class T>
 __device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
     if constexpr (MODE == GAMER_MODE_MIXED) {
         const double a = m1, b = m2, c = m3;
-        return r > T(0) && (double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0;
+        return (r > T(0)) & ((double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0);
     } else if constexpr (MODE == GAMER_MODE_FF) {
         float se, ee, t;
         const float s = sq3_ff(m1, m2, m3, se);
         const float re = two_prod(r, E, ee);
         const float d = two_sum(re, -0.5f * s, t);
-        return r > 0.0f && (d + ((ee - 0.5f * se) + t)) > 0.0f;
+        return (r > 0.0f) & ((d + ((ee - 0.5f * se) + t)) > 0.0f);
     } else {
-        return r > T(0) && (r * E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3)) > T(0);
+        return (r > T(0)) & ((r * E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3)) > T(0));
     }
 }
 
@@ -586,7 +586,7 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
     for (int f = 0; f < 6; ++f) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
-        ok = ok && admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4]);
+        ok &= admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4]);
     }
     return ok;
 }
@@ -625,15 +625,22 @@ __device__ __forceinline__ bool is_read_cell(int i, int j, int k) {
     return o <= 1 || (o == 2 && ni && nj && nk);
 }
 
-// Which of this thread's plane cells (c = tid + r * kThreads, r < 3) the
-// stencil reads, for the three kinds of plane (bit 3 * kind + r): kind 0 a
-// plane inside the group, 1 one plane outside (-1, 16), 2 two outside (-2, 17).
+// Plane cell of this thread's r-th conversion (r = 0, 1, 2), or -1: cell
+// tid + r * kThreads while inside the plane.
+__device__ __forceinline__ int convert_cell(int r) {
+    const int c = int(threadIdx.x) + r * kThreads;
+    return c < kPlane ? c : -1;
+}
+
+// Which of this thread's plane cells (convert_cell(r), r < 3) the stencil
+// reads, for the three kinds of plane (bit 3 * kind + r): kind 0 a plane
+// inside the group, 1 one plane outside (-1, 16), 2 two outside (-2, 17).
 __device__ __forceinline__ uint32_t read_cell_mask() {
     uint32_t m = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const int c = int(threadIdx.x) + r * kThreads;
-        if (c >= kPlane) break;
+        const int c = convert_cell(r);
+        if (c < 0) break;
         const int i = c % 20 - 2, j = c / 20 - 2;
         if (is_read_cell(i, j, 0)) m |= 1u << r;
         if (is_read_cell(i, j, -1)) m |= 1u << (3 + r);
@@ -648,16 +655,16 @@ __device__ __forceinline__ uint32_t plane_read_bits(uint32_t mask, int kp) {
     return (mask >> (3 * kind)) & 7u;
 }
 
-// Conserved plane -> primitive plane (all 400 cells; the flag covers the read
-// cells, `rbits` from plane_read_bits).
+// Conserved plane -> primitive plane (all 400 cells, by convert_cell; the
+// flag covers the read cells, `rbits` from plane_read_bits).
 template <int MODE, class T, class P>
 __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W,
                                               uint32_t rbits, const KConst<T, P>& kc,
                                               uint32_t& st) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const int c = int(threadIdx.x) + r * kThreads;
-        if (c >= kPlane) break;
+        const int c = convert_cell(r);
+        if (c < 0) break;
         T u[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) u[q] = U[q * kPlane + c];
