@@ -40,11 +40,28 @@ struct DeviceInfo {
     int device = -1;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
+    int smem_per_sm = 0;     // shared memory an SM can give its blocks (bytes)
+    int smem_reserved = 0;   // shared memory the system reserves per block (bytes)
     int status = GAMER_E_CUDA;
 };
 
 // Properties of the current device (cached per device id).
 DeviceInfo current_device();
+
+// Carveout preference (percent of smem_per_sm) for blocks that need `need`
+// bytes of shared memory per SM in all: the floor of the percentage of the
+// smallest shared-memory capacity of the sm_100 family (0, 8, 16, 32, 64,
+// 100, 132, 164, 196 or 228 KB) that holds them, which the driver's
+// rounding up maps back to that capacity; 100 when only the largest does.
+inline int carveout_percent(int64_t need, int smem_per_sm) {
+    static const int kCapacityKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+    if (smem_per_sm <= 0) return 100;
+    for (int kb : kCapacityKB) {
+        const int64_t cap = int64_t(kb) * 1024;
+        if (cap >= need && cap < smem_per_sm) return int(100 * cap / smem_per_sm);
+    }
+    return 100;
+}
 
 inline int device_ok() {
     DeviceInfo d = current_device();

@@ -41,7 +41,6 @@ namespace gamer {
 constexpr int kThreads = 160;
 constexpr int kPlane = 400;       // 20 x 20 cells per input plane
 constexpr int kFaceStride = 288;  // 16^2 interior, 16 slab entries, 16 write-only entries
-constexpr int kFluxStride = 544;  // 16 x 17 x-faces + 17 x 16 y-faces
 
 template <int MODE> struct Prec;
 template <> struct Prec<GAMER_MODE_F32> { using T = float; using P = float; };
@@ -78,9 +77,11 @@ template <class T, int RING = 2>
 struct alignas(16) Smem {
     T raw[RING][5 * kPlane + 4];  // ring of conserved input planes (TMA / cp.async)
     T W[3][5 * kPlane];    // primitive planes
+    // face states of the x/y faces; after a face's Riemann solve, its flux
+    // in both state slots the solve consumed (each slot feeds one solve), so
+    // the owner of a cell finds F(i -/+ 1/2) in its own xm / xp slots (y
+    // alike).  The group epilogue's per-warp partials reuse xm.
     T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
-    T fxy[5 * kFluxStride];  // x- and y-face fluxes of the current plane
-    double red[kThreads / 32][6];
     uint64_t mbar[RING];
     uint32_t status;
 };
@@ -97,7 +98,7 @@ struct KConst {
     T gm1_lo;           // gamma - 1 - gm1: the float-float mode's low part
 };
 
-// row slot of a 16-wide face / flux array (see the bank note above)
+// row slot of a 16-wide face array (see the bank note above)
 __device__ __forceinline__ int frow(int j) { return j ^ ((j >> 2) & 1); }
 
 // Face-flux plane of the face at cell index b in [0, 16] along direction dir
@@ -273,7 +274,8 @@ __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KCons
     const T is1 = rcp_(s1r), is4 = rcp_(s4r);
     const T p1 = pressure<MODE>(s1r, s1n, s1a, s1b, s1E, is1, kc);
     const T p4 = pressure<MODE>(s4r, s4n, s4a, s4b, s4E, is4, kc);
-    const bool fallback = !(cT2 > T(0) && s1r > T(0) && p1 > T(0) && s4r > T(0) && p4 > T(0));
+    const bool fallback =
+        !((cT2 > T(0)) & (s1r > T(0)) & (p1 > T(0)) & (s4r > T(0)) & (p4 > T(0)));
     const T l1s = s1n * is1 - sqrt_(kc.gamma * p1 * is1);
     const T l5s = s4n * is4 + sqrt_(kc.gamma * p4 * is4);
     const T d1 = max_(T(0), max_(K1u - (uL - cL), l1s - K1u));
@@ -674,12 +676,10 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
         W[2 * kPlane + c] = u[2] * ir;
         W[3 * kPlane + c] = u[3] * ir;
         W[4 * kPlane + c] = pressure<MODE>(u[0], u[1], u[2], u[3], u[4], ir, kc);
-        if ((rbits >> r) & 1u) {
-            bool fin = true;
+        bool fin = true;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) fin = fin && finite_(u[q]);
-            if (!fin) st |= GAMER_ST_BAD_INPUT;
-        }
+        for (int q = 0; q < 5; ++q) fin &= finite_(u[q]);
+        if (!fin & bool((rbits >> r) & 1u)) st |= GAMER_ST_BAD_INPUT;
     }
 }
 
@@ -1024,9 +1024,11 @@ __global__ void __launch_bounds__(kThreads, MINB)
             // divergence of plane k-1 from the fluxes of phase B(k-1) -- then
             // A(k), the half-step prediction of plane k; phase B(k) solves the
             // z faces k-1/2, which completes plane k-1 (written out at once),
-            // then the x/y faces of plane k, and converts plane k+2.  C only
-            // reads what B wrote and A only writes what B reads next, so C(k-1)
-            // and A(k) share a phase.  Across the x/y solves only U, the lower
+            // then the x/y faces of plane k, and converts plane k+2.  C reads
+            // only the thread's own face slots (where B left the fluxes), which
+            // its own A overwrites next, and A writes nothing another thread
+            // reads before the barrier, so C(k-1) and A(k) share a phase.
+            // Across the x/y solves only U, the lower
             // z flux and the z+ state of plane k stay in registers.  The two z
             // fluxes of a cell are differenced before scaling, so equal fluxes
             // cancel exactly (a uniform state stays bitwise uniform).
@@ -1041,11 +1043,11 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 if (kc.floors) apply_floors<MODE>(o, ir, p, kc, st);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) gout[((q * 16 + kk) * 16 + jj) * 16 + i0] = o[q];
-                if (!(o[0] > T(0)) || !(p > T(0))) st |= GAMER_ST_NONPOSITIVE_OUT;
+                if (!((o[0] > T(0)) & (p > T(0)))) st |= GAMER_ST_NONPOSITIVE_OUT;
                 const T c2 = kc.gamma * p * ir;
                 const T cs = (c2 > T(0)) ? sqrt_(c2) : T(0);
                 const T sp = max_(max_(abs_(o[1] * ir), abs_(o[2] * ir)), abs_(o[3] * ir)) + cs;
-                if (sp > smax) smax = sp;
+                smax = (sp > smax) ? sp : smax;
 #pragma unroll
                 for (int q = 0; q < 5; ++q) sums.add(q, o[q]);
             };
@@ -1061,16 +1063,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (cc == 1 && !two) break;
-                        const int jj = cc ? j1 : j0;
                         const int fa = cc ? fa1 : fa0;
-                        const int rxp = (i0 == 15) ? (256 + jj) : (fa + 1);
-                        const int ryp = 272 + ((jj == 15) ? (256 + i0) : (frow(jj + 1) * 16 + i0));
                         const T* uc = cc ? uc1 : uc0;
                         T* Ec = cc ? E1 : E0;
 #pragma unroll
                         for (int q = 0; q < 5; ++q) {
-                            const T* fq = S.fxy + q * kFluxStride;
-                            const T D = (fq[rxp] - fq[fa]) + (fq[ryp] - fq[272 + fa]);
+                            const int o = q * kFaceStride + fa;
+                            const T D = (S.xp[o] - S.xm[o]) + (S.yp[o] - S.ym[o]);
                             Ec[q] = uc[q] - lam * D;
                         }
                     }
@@ -1172,14 +1171,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     for (int r = 0; r < nxy; ++r) {
                         const int it = two ? (r * 96 + tid) : (288 + r * 64 + (tid - 96));
                         const bool isy = it >= 272;
-                        int lo, hi, wr, a, b;
-                        const T *LA, *RA;
+                        int lo, hi, a, b;
+                        T *LA, *RA;
                         if (!isy) {
                             const int j = it / 17, f = it - j * 17;
                             const int rj = frow(j) * 16;
                             lo = (f == 0) ? (256 + j) : (rj + f - 1);
                             hi = (f == 16) ? (256 + j) : (rj + f);
-                            wr = hi;
                             LA = S.xp;
                             RA = S.xm;
                             a = j;
@@ -1188,7 +1186,6 @@ __global__ void __launch_bounds__(kThreads, MINB)
                             const int y = it - 272, f = y >> 4, i = y & 15;
                             lo = (f == 0) ? (256 + i) : (frow(f - 1) * 16 + i);
                             hi = (f == 16) ? (256 + i) : (frow(f) * 16 + i);
-                            wr = 272 + hi;
                             LA = S.yp;
                             RA = S.ym;
                             a = i;
@@ -1208,11 +1205,17 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         R[3] = RA[c3 * kFaceStride + hi];
                         R[4] = RA[4 * kFaceStride + hi];
                         roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
-                        S.fxy[wr] = F[0];
-                        S.fxy[c1 * kFluxStride + wr] = F[1];
-                        S.fxy[c2 * kFluxStride + wr] = F[2];
-                        S.fxy[c3 * kFluxStride + wr] = F[3];
-                        S.fxy[4 * kFluxStride + wr] = F[4];
+                        // the flux into the two state slots this solve consumed
+                        LA[lo] = F[0];
+                        LA[c1 * kFaceStride + lo] = F[1];
+                        LA[c2 * kFaceStride + lo] = F[2];
+                        LA[c3 * kFaceStride + lo] = F[3];
+                        LA[4 * kFaceStride + lo] = F[4];
+                        RA[hi] = F[0];
+                        RA[c1 * kFaceStride + hi] = F[1];
+                        RA[c2 * kFaceStride + hi] = F[2];
+                        RA[c3 * kFaceStride + hi] = F[3];
+                        RA[4 * kFaceStride + hi] = F[4];
                         const int face = flux_plane(isy ? 1 : 0, b, kc.flux9);
                         if (gff && face >= 0) {
                             // x planes: [v][k][j];  y planes: [v][k][i]
@@ -1252,10 +1255,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 for (int q = 0; q < 5; ++q) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], off);
             }
             const uint32_t wst = __reduce_or_sync(0xffffffffu, st);
+            // per-warp partials in the x- face array (no face state is live
+            // between a group's last phase and the next group's first one)
+            double(*red)[6] = reinterpret_cast<double(*)[6]>(S.xm);
             if (lane == 0) {
-                S.red[warp][0] = dmax;
+                red[warp][0] = dmax;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) S.red[warp][1 + q] = dsum[q];
+                for (int q = 0; q < 5; ++q) red[warp][1 + q] = dsum[q];
                 if (wst) atomicOr(&S.status, wst);
             }
             __syncthreads();
@@ -1263,8 +1269,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 if (partials) {
                     double m = 0.0, s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
                     for (int w = 0; w < kThreads / 32; ++w) {
-                        m = fmax(m, S.red[w][0]);
-                        for (int q = 0; q < 5; ++q) s[q] += S.red[w][1 + q];
+                        m = fmax(m, red[w][0]);
+                        for (int q = 0; q < 5; ++q) s[q] += red[w][1 + q];
                     }
                     partials[g * 6] = m;
                     for (int q = 0; q < 5; ++q) partials[g * 6 + 1 + q] = s[q];

@@ -148,6 +148,17 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         per_sm < 1)
         return GAMER_E_CUDA;
     if (want > 0 && want < per_sm && !special) per_sm = want;
+    // Shared memory the SM does not give to these blocks stays L1 cache (for
+    // the register spills above all): ask for the smallest carveout that holds
+    // per_sm blocks.  The driver rounds a carveout percentage up to the next
+    // capacity it supports; passing the floor of that capacity's own
+    // percentage selects exactly it.
+    const int pct = carveout_percent(int64_t(per_sm) * (smem + dev.smem_reserved),
+                                     dev.smem_per_sm);
+    if (pct < 100 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct) !=
+            cudaSuccess)
+        return GAMER_E_CUDA;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
     kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh, status,
                                                             partials, N, kc, geo);
