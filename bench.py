@@ -431,49 +431,52 @@ def main():
     for g in graphs:
         g.close()
 
-    # end to end: the same level held in pinned HOST memory, one public call per
-    # step (gamer_pipeline_level_step_host: z-slabs of the level's interiors
-    # with a halo layer each side go to the device, the ghost zones are
-    # gathered there, results and partials come back); the next dt is the
-    # FP64 max over the returned partials, on the host
+    # end to end: the same level held in pinned HOST memory, advanced through
+    # the public multi-step call (gamer_pipeline_level_run_host): every step
+    # copies the level's interiors in and the new state out (z-slabs through a
+    # device copy of the level, ghost zones gathered on the device), the next
+    # step's copies in overlapping this step's copies out; the dt of each step
+    # after the first is the FP64 CFL reduction of the previous step's
+    # partials on the device (the first from the partials of U^0)
     e2e = None
     if not args.no_e2e:
         h_lv = [torch.from_numpy(level_h).to(T).pin_memory(),
                 torch.empty((G, 5, 16, 16, 16), dtype=T).pin_memory()]
         h_st = torch.empty(G, dtype=torch.int32).pin_memory()
         h_part = torch.empty((G, 6), dtype=torch.float64).pin_memory()
+        h_dt = torch.empty(max(args.steps, 50), dtype=torch.float64).pin_memory()
+        pre = native.Pipeline(mode, G, with_flux=False)
+        pre.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 0.0, dh, h_st, h_part, params)
+        pre.close()
+        dt0 = CFL * dh / float(h_part[:, 0].max())
         timing = {}
         for batch in (256, 512, 1024, 2048):             # slabs of 1, 2, 4, 8 layers
             pl = native.Pipeline(mode, batch, with_flux=False)
-            pl.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 0.0, dh, h_st, h_part, params)
+            pl.level_run_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 2, dt0, dh, CFL, params)
             t0 = time.perf_counter()
-            for _ in range(3):
-                pl.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 1e-4, dh, h_st, h_part,
-                                   params)
+            pl.level_run_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 4, dt0, dh, CFL, params)
             timing[batch] = time.perf_counter() - t0
             pl.close()
         batch = min(timing, key=timing.get)
         pipe = native.Pipeline(mode, batch, with_flux=False)
-        pipe.level_step_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 0.0, dh, h_st, h_part, params)
-        cur = 0
+        pipe.level_run_host(h_lv[0], h_lv[1], gx, gy, gz, 0, 2, dt0, dh, CFL, params)
         n_e2e = max(3, min(args.steps, 50))
         dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            dt_e = CFL * dh / float(h_part[:, 0].max())
-            pipe.level_step_host(h_lv[cur], h_lv[1 - cur], gx, gy, gz, 0, dt_e, dh, h_st,
-                                 h_part, params)
-            cur = 1 - cur
+        pipe.level_run_host(h_lv[0], h_lv[1], gx, gy, gz, 0, n_e2e, dt0, dh, CFL, params,
+                            h_dt[:n_e2e], h_st, h_part)
         el_e2e = dist.max_over_ranks(time.perf_counter() - t0, device=dev)
         h2d, d2h = pipe.last_bytes()
         pipe.close()
         e2e = {"value": world * cells_per_step * n_e2e / el_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
                "steps": n_e2e, "slab_groups": batch,
-               "api": "gamer_pipeline_level_step_host (pinned host level streamed in z-slabs "
-                      "of %d layers through a device copy of the level, each layer once; "
-                      "ghost gather on the device; 3 streams; state, status and partials "
-                      "back)" % (batch // (gx * gy))}
+               "api": "gamer_pipeline_level_run_host (%d steps of the pinned host level in one "
+                      "call; each step copies the interiors in and the new state out in z-slabs "
+                      "of %d layers through a device copy of the level, ghost gather on the "
+                      "device, the next step's copies in overlapping this step's copies out; "
+                      "dt per step from the previous step's partials on the device; status and "
+                      "last partials back at the end)" % (n_e2e, batch // (gx * gy))}
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6702.2)

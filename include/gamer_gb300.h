@@ -346,7 +346,7 @@ int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds);
  * every layer crosses the link once per step.
  *
  * gamer_pipeline_last_bytes: host->device and device->host bytes the last
- * advance_host or level_step_host call on this pipeline copied.
+ * advance_host, level_step_host or level_run_host call on this pipeline copied.
  *
  * gamer_pipeline_set_level_mode: 0 automatic (default), 1 always the device
  * copy of the level, 2 always slab windows with halo layers (frees the copy).
@@ -357,6 +357,37 @@ int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* level_in_host
                                    double* partials_host, const gh_params* p, int32_t nthreads);
 int gamer_pipeline_last_bytes(const gamer_pipeline* pl, int64_t* h2d, int64_t* d2h);
 int gamer_pipeline_set_level_mode(gamer_pipeline* pl, int32_t mode);
+
+/*
+ * gamer_pipeline_level_run_host: nsteps steps of a uniform level that lives in
+ * HOST memory (paper Sec. 3: transfers overlapped with computation, here also
+ * from one step to the next).  Step n reads level[n % 2] and writes
+ * level[(n + 1) % 2] (level0, level1: [G][5][16]^3 host arrays, G =
+ * gx*gy*gz, element type by mode, not overlapping, pinned for overlap); the
+ * final state is in level[nsteps % 2].  Every step copies its input to the
+ * device and its result back, in z-slabs of L layers as
+ * gamer_pipeline_level_step_host with a device copy of the level; step n
+ * takes its slabs in the order n, n+1, ... (mod the slab count), so a slab's
+ * copy in waits only for the previous step's copy out of the same slab, and
+ * the next step's copies in overlap this step's copies out.
+ * Time step: dt0 (finite, >= 0) for step 0, e.g. from the partials of a
+ * previous call; for n >= 1, cfl * dh / max_g partials[g][0] of step n-1
+ * (gamer_hydro_dt on the device, the FP64 formula a host would use).
+ * dh finite > 0, cfl finite > 0, nsteps >= 0, bc 0 periodic or 1
+ * zero-gradient, extents as gamer_hydro_advance_level_*.
+ *   dt_host       [nsteps] the dt of every step, or NULL.
+ *   status_host   [G] GAMER_ST_* bits OR-ed over the steps, or NULL.
+ *   partials_host [G][6] partials of the last step, or NULL.
+ * Device memory: four copies of the level (input and output per step
+ * parity) and per-group scratch, allocated on first use and held until
+ * gamer_pipeline_destroy; GAMER_E_CUDA when they do not fit.  One bounded
+ * wait at the end (the pipeline timeout times nsteps).  gamer_pipeline_last_bytes
+ * reports the call's total bytes.
+ */
+int gamer_pipeline_level_run_host(gamer_pipeline* pl, void* level0, void* level1, int32_t gx,
+                                  int32_t gy, int32_t gz, int32_t bc, int32_t nsteps, double dt0,
+                                  double dh, double cfl, double* dt_host, uint32_t* status_host,
+                                  double* partials_host, const gh_params* p);
 
 /*
  * gamer_fill_ghosts_uniform_host_{f32,f64}: gamer_fill_ghosts_uniform_* on

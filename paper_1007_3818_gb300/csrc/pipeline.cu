@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <climits>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -45,6 +47,12 @@ extern "C" int gamer_hydro_advance_level_window_f64(const double*, double*, doub
                                                     int32_t, int32_t, const double*,
                                                     const double*, uint32_t*, double*,
                                                     const gh_params*, void*);
+
+extern "C" size_t gamer_hydro_dt_workspace_bytes(int64_t N, int32_t n_levels);
+extern "C" int gamer_hydro_dt(const double* partials, int64_t N, const int32_t* level,
+                              int32_t n_levels, const double* dh_level, double cfl, double* dt_out,
+                              double* totals, double* dt_group, void* workspace,
+                              size_t workspace_bytes, void* stream);
 
 namespace {
 
@@ -93,12 +101,58 @@ struct gamer_pipeline {
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     BufSet set[kSets];
     double timeout_s = 60.0;
+    // multi-step runs (level_run_host): device input and output levels by
+    // step parity, per-group dt and dh, status of the step and its OR over
+    // the steps, partials, dh and the dt of every step, dt workspace, and
+    // events [parity][in, out][slab] for the copies of each slab
+    void* run_in[2] = {nullptr, nullptr};
+    void* run_out[2] = {nullptr, nullptr};
+    double* run_dt = nullptr;        // [2][G]: dt, dh per group
+    uint32_t* run_status = nullptr;  // [2][G]: this step, OR over the steps
+    double* run_partials = nullptr;  // [G][6]
+    double* run_aux = nullptr;       // [1 + steps]: dh, then the dt of each step
+    void* run_ws = nullptr;
+    size_t run_ws_bytes = 0, run_cap = 0, run_level_bytes = 0, run_aux_cap = 0;
+    cudaEvent_t* run_ev = nullptr;   // [2][2][run_ev_slabs]
+    int32_t run_ev_slabs = 0;
+    cudaEvent_t run_comp[2] = {nullptr, nullptr};
+    cudaEvent_t run_end = nullptr;
 };
 
 namespace {
 
+void release_run(gamer_pipeline* pl) {
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(pl->run_in[i]);
+        cudaFree(pl->run_out[i]);
+        pl->run_in[i] = pl->run_out[i] = nullptr;
+    }
+    cudaFree(pl->run_dt);
+    cudaFree(pl->run_status);
+    cudaFree(pl->run_partials);
+    cudaFree(pl->run_aux);
+    cudaFree(pl->run_ws);
+    pl->run_dt = pl->run_partials = pl->run_aux = nullptr;
+    pl->run_status = nullptr;
+    pl->run_ws = nullptr;
+    pl->run_ws_bytes = pl->run_cap = pl->run_level_bytes = pl->run_aux_cap = 0;
+    if (pl->run_ev) {
+        for (int32_t i = 0; i < 4 * pl->run_ev_slabs; ++i)
+            if (pl->run_ev[i]) cudaEventDestroy(pl->run_ev[i]);
+        delete[] pl->run_ev;
+        pl->run_ev = nullptr;
+    }
+    pl->run_ev_slabs = 0;
+    for (auto& ev : pl->run_comp)
+        if (ev) cudaEventDestroy(ev);
+    pl->run_comp[0] = pl->run_comp[1] = nullptr;
+    if (pl->run_end) cudaEventDestroy(pl->run_end);
+    pl->run_end = nullptr;
+}
+
 void release(gamer_pipeline* pl) {
     if (!pl) return;
+    release_run(pl);
     if (pl->stage_dt) cudaFreeHost(pl->stage_dt);
     cudaFree(pl->lev_in);
     cudaFree(pl->lev_out);
@@ -566,6 +620,257 @@ extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* le
         S.used = true;
     }
     return wait_event(pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
+}
+
+namespace {
+
+__global__ void status_or_kernel(uint32_t* __restrict__ acc, const uint32_t* __restrict__ st,
+                                 int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        acc[i] |= st[i];
+}
+
+// Device buffers and events of a run over G groups (level_bytes per level),
+// nslab slabs and nsteps steps; grown when a run needs more.
+bool ensure_run(gamer_pipeline* pl, int64_t G, size_t level_bytes, int32_t nslab,
+                int32_t nsteps) {
+    if (pl->run_cap < size_t(G) || pl->run_level_bytes < level_bytes) {
+        release_run(pl);
+        bool ok = true;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaMalloc(&pl->run_in[i], level_bytes) == cudaSuccess &&
+                 cudaMalloc(&pl->run_out[i], level_bytes) == cudaSuccess;
+        const size_t ws = gamer_hydro_dt_workspace_bytes(G, 1);
+        ok = ok &&
+             cudaMalloc(reinterpret_cast<void**>(&pl->run_dt), size_t(G) * 16) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&pl->run_status), size_t(G) * 8) ==
+                 cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&pl->run_partials), size_t(G) * 48) ==
+                 cudaSuccess &&
+             ws > 0 && cudaMalloc(&pl->run_ws, ws) == cudaSuccess;
+        for (auto& ev : pl->run_comp)
+            ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&pl->run_end, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            release_run(pl);
+            return false;
+        }
+        pl->run_ws_bytes = ws;
+        pl->run_cap = size_t(G);
+        pl->run_level_bytes = level_bytes;
+    }
+    if (pl->run_aux_cap < size_t(nsteps) + 1) {
+        cudaFree(pl->run_aux);
+        pl->run_aux = nullptr;
+        pl->run_aux_cap = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&pl->run_aux), (size_t(nsteps) + 1) * 8) !=
+            cudaSuccess)
+            return false;
+        pl->run_aux_cap = size_t(nsteps) + 1;
+    }
+    if (pl->run_ev_slabs < nslab) {
+        if (pl->run_ev) {
+            for (int32_t i = 0; i < 4 * pl->run_ev_slabs; ++i)
+                if (pl->run_ev[i]) cudaEventDestroy(pl->run_ev[i]);
+            delete[] pl->run_ev;
+        }
+        pl->run_ev_slabs = 0;
+        pl->run_ev = new (std::nothrow) cudaEvent_t[4 * size_t(nslab)]();
+        if (!pl->run_ev) return false;
+        for (int32_t i = 0; i < 4 * nslab; ++i)
+            if (cudaEventCreateWithFlags(&pl->run_ev[i], cudaEventDisableTiming) != cudaSuccess)
+                return false;
+        pl->run_ev_slabs = nslab;
+    }
+    return true;
+}
+
+int advance_window(const gamer_pipeline* pl, const void* din, void* out, int32_t gx, int32_t gy,
+                   int32_t gz, int32_t bc, int32_t z0, int32_t nz, const double* dt,
+                   const double* dh, uint32_t* status, double* partials, const gh_params* p) {
+    if (pl->mode == GAMER_MODE_F32)
+        return gamer_hydro_advance_level_window_f32((const float*)din, (float*)out, nullptr, gx,
+                                                    gy, gz, bc, 0, gz, z0, nz, dt, dh, status,
+                                                    partials, p, pl->s_comp);
+    if (pl->mode == GAMER_MODE_MIXED)
+        return gamer_hydro_advance_level_window_mixed((const float*)din, (float*)out, nullptr,
+                                                      gx, gy, gz, bc, 0, gz, z0, nz, dt, dh,
+                                                      status, partials, p, pl->s_comp);
+    if (pl->mode == GAMER_MODE_FF)
+        return gamer_hydro_advance_level_window_ff((const float*)din, (float*)out, nullptr, gx,
+                                                   gy, gz, bc, 0, gz, z0, nz, dt, dh, status,
+                                                   partials, p, pl->s_comp);
+    return gamer_hydro_advance_level_window_f64((const double*)din, (double*)out, nullptr, gx, gy,
+                                                gz, bc, 0, gz, z0, nz, dt, dh, status, partials,
+                                                p, pl->s_comp);
+}
+
+}  // namespace
+
+// nsteps steps of a host level between two host buffers.  Step n's slabs go
+// in the order n, n+1, ... (mod the slab count), so that its first slabs read
+// what step n-1 sent back first; copies in of step n wait only for step
+// n-1's copies out of the same slabs, and both link directions stay busy
+// across steps.  The dt of step n >= 1 is reduced on the device from step
+// n-1's partials (gamer_hydro_dt), on the compute stream.
+extern "C" int gamer_pipeline_level_run_host(gamer_pipeline* pl, void* level0, void* level1,
+                                             int32_t gx, int32_t gy, int32_t gz, int32_t bc,
+                                             int32_t nsteps, double dt0, double dh, double cfl,
+                                             double* dt_host, uint32_t* status_host,
+                                             double* partials_host, const gh_params* p) {
+    using namespace gamer;
+    if (!pl) return GAMER_E_NULL;
+    int rc = check_params(p);
+    if (rc != GAMER_OK) return rc;
+    if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1) || nsteps < 0) return GAMER_E_PARAM;
+    if (!(std::isfinite(dt0) && dt0 >= 0.0) || !(std::isfinite(dh) && dh > 0.0) ||
+        !(std::isfinite(cfl) && cfl > 0.0))
+        return GAMER_E_PARAM;
+    if (int64_t(gx) * 16 > (1 << 30) || int64_t(gy) * 16 > (1 << 30) ||
+        int64_t(gz) * 16 > (1 << 30) || int64_t(gx) * gy * 1280 + 2048 > INT32_MAX)
+        return GAMER_E_PARAM;
+    pl->h2d_bytes = pl->d2h_bytes = 0;
+    const int64_t layer = int64_t(gx) * gy;
+    const int64_t G = layer * gz;
+    if (G == 0 || nsteps == 0) return GAMER_OK;
+    if (!level0 || !level1) return GAMER_E_NULL;
+    const size_t e = pl->esz;
+    const size_t layer_bytes = size_t(layer) * 20480 * e;
+    const size_t level_bytes = layer_bytes * size_t(gz);
+    if (overlaps(level0, level_bytes, level1, level_bytes)) return GAMER_E_OVERLAP;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != pl->device) return GAMER_E_DEVICE;
+    const int32_t L = int32_t(std::max<int64_t>(1, std::min<int64_t>(pl->batch / layer, gz)));
+    const int32_t nslab = (gz + L - 1) / L;
+    if (!ensure_run(pl, G, level_bytes, nslab, nsteps)) {
+        cudaGetLastError();
+        return GAMER_E_CUDA;
+    }
+    // dt0 and dh of every group through the pinned staging
+    if (pl->stage_n < size_t(G)) {
+        if (pl->stage_dt) cudaFreeHost(pl->stage_dt);
+        pl->stage_dt = nullptr;
+        pl->stage_n = 0;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pl->stage_dt), size_t(G) * 16,
+                          cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return GAMER_E_CUDA;
+        }
+        pl->stage_n = size_t(G);
+    }
+    const size_t cnt = pl->stage_n;
+    for (int64_t i = 0; i < G; ++i) {
+        pl->stage_dt[i] = dt0;
+        pl->stage_dt[cnt + i] = dh;
+    }
+    // the previous call's copies out of the staging are complete (it returned
+    // after its last copy), so the staging may be rewritten here
+    bool ok = cudaMemcpyAsync(pl->run_dt, pl->stage_dt, size_t(G) * 8, cudaMemcpyHostToDevice,
+                              pl->s_h2d) == cudaSuccess &&
+              cudaMemcpyAsync(pl->run_dt + G, pl->stage_dt + cnt, size_t(G) * 8,
+                              cudaMemcpyHostToDevice, pl->s_h2d) == cudaSuccess &&
+              cudaMemcpyAsync(pl->run_aux, pl->stage_dt + cnt, 8, cudaMemcpyHostToDevice,
+                              pl->s_h2d) == cudaSuccess &&
+              cudaMemcpyAsync(pl->run_aux + 1, pl->stage_dt, 8, cudaMemcpyHostToDevice,
+                              pl->s_h2d) == cudaSuccess &&
+              cudaMemsetAsync(pl->run_status + G, 0, size_t(G) * 4, pl->s_comp) == cudaSuccess;
+    if (!ok) return GAMER_E_CUDA;
+    pl->h2d_bytes += 16 * G + 16;
+    char* hbuf[2] = {static_cast<char*>(level0), static_cast<char*>(level1)};
+    const DeviceInfo d = current_device();
+    const unsigned or_blocks =
+        unsigned(std::min<int64_t>((G + 255) / 256, int64_t(d.sm_count > 0 ? d.sm_count : 1) * 8));
+    for (int32_t n = 0; n < nsteps; ++n) {
+        const int par = n & 1;
+        const char* hin = hbuf[par];
+        char* hout = hbuf[par ^ 1];
+        char* din = static_cast<char*>(pl->run_in[par]);
+        char* dout = static_cast<char*>(pl->run_out[par]);
+        cudaEvent_t* ev_in = pl->run_ev + size_t(par * 2 + 0) * pl->run_ev_slabs;
+        cudaEvent_t* ev_out = pl->run_ev + size_t(par * 2 + 1) * pl->run_ev_slabs;
+        cudaEvent_t* prev_out = pl->run_ev + size_t((par ^ 1) * 2 + 1) * pl->run_ev_slabs;
+        const int32_t r = n % nslab;  // first slab of this step
+        // copies in.  This parity's device input was last read by step n-2's
+        // kernels; the host input of a slab is step n-1's output of it.
+        if (n >= 2 && cudaStreamWaitEvent(pl->s_h2d, pl->run_comp[par], 0) != cudaSuccess)
+            return GAMER_E_CUDA;
+        // the layer below slab r first (periodic wrap, or r > 0): it is the
+        // top layer of the last slab in this step's order, r - 1
+        const bool below = nslab > 1 && (bc == 0 || r > 0);
+        const int32_t sbelow = (r + nslab - 1) % nslab;
+        if (below) {
+            const size_t off = size_t((int64_t(r) * L + gz - 1) % gz) * layer_bytes;
+            ok = (n == 0 || cudaStreamWaitEvent(pl->s_h2d, prev_out[sbelow], 0) == cudaSuccess) &&
+                 cudaMemcpyAsync(din + off, hin + off, layer_bytes, cudaMemcpyHostToDevice,
+                                 pl->s_h2d) == cudaSuccess;
+            if (!ok) return GAMER_E_CUDA;
+            pl->h2d_bytes += int64_t(layer_bytes);
+        }
+        for (int32_t i = 0; i < nslab; ++i) {
+            const int32_t s = (r + i) % nslab;
+            const int32_t z0 = s * L, nz = std::min<int32_t>(L, gz - z0);
+            const int32_t cz = (below && s == sbelow) ? nz - 1 : nz;
+            const size_t off = size_t(z0) * layer_bytes, bytes = size_t(cz) * layer_bytes;
+            ok = (n == 0 || cudaStreamWaitEvent(pl->s_h2d, prev_out[s], 0) == cudaSuccess) &&
+                 (bytes == 0 || cudaMemcpyAsync(din + off, hin + off, bytes,
+                                                cudaMemcpyHostToDevice, pl->s_h2d) ==
+                                    cudaSuccess) &&
+                 cudaEventRecord(ev_in[i], pl->s_h2d) == cudaSuccess;
+            if (!ok) return GAMER_E_CUDA;
+            pl->h2d_bytes += int64_t(bytes);
+        }
+        // this step's dt: dt0, or reduced from step n-1's partials
+        if (n >= 1) {
+            rc = gamer_hydro_dt(pl->run_partials, G, nullptr, 1, pl->run_aux, cfl,
+                                pl->run_aux + 1 + n, nullptr, pl->run_dt, pl->run_ws,
+                                pl->run_ws_bytes, pl->s_comp);
+            if (rc != GAMER_OK) return rc;
+        }
+        for (int32_t i = 0; i < nslab; ++i) {
+            const int32_t s = (r + i) % nslab;
+            const int32_t z0 = s * L, nz = std::min<int32_t>(L, gz - z0);
+            const int64_t g0 = int64_t(z0) * layer, ng = int64_t(nz) * layer;
+            // its layers and the layer above are in copies 0 .. i+1; its
+            // output slot was last read by step n-2's copy out
+            ok = cudaStreamWaitEvent(pl->s_comp, ev_in[std::min(i + 1, nslab - 1)], 0) ==
+                     cudaSuccess &&
+                 (n < 2 || cudaStreamWaitEvent(pl->s_comp, ev_out[s], 0) == cudaSuccess);
+            if (!ok) return GAMER_E_CUDA;
+            rc = advance_window(pl, din, dout + size_t(g0) * 20480 * e, gx, gy, gz, bc, z0, nz,
+                                pl->run_dt + g0, pl->run_dt + G + g0, pl->run_status + g0,
+                                pl->run_partials + g0 * 6, p);
+            if (rc != GAMER_OK) return rc;
+            BufSet& S = pl->set[i % kSets];
+            ok = cudaEventRecord(S.comp_done, pl->s_comp) == cudaSuccess &&
+                 cudaStreamWaitEvent(pl->s_d2h, S.comp_done, 0) == cudaSuccess &&
+                 cudaMemcpyAsync(hout + size_t(z0) * layer_bytes, dout + size_t(z0) * layer_bytes,
+                                 size_t(nz) * layer_bytes, cudaMemcpyDeviceToHost,
+                                 pl->s_d2h) == cudaSuccess &&
+                 cudaEventRecord(ev_out[s], pl->s_d2h) == cudaSuccess;
+            if (!ok) return GAMER_E_CUDA;
+            pl->d2h_bytes += ng * 20480 * int64_t(e);
+            S.used = true;
+        }
+        status_or_kernel<<<or_blocks, 256, 0, pl->s_comp>>>(pl->run_status + G, pl->run_status,
+                                                           G);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaEventRecord(pl->run_comp[par], pl->s_comp) != cudaSuccess)
+            return GAMER_E_CUDA;
+    }
+    // the run's dt sequence, status bits OR-ed over the steps, last partials
+    ok = cudaStreamWaitEvent(pl->s_d2h, pl->run_comp[(nsteps - 1) & 1], 0) == cudaSuccess &&
+         (!dt_host || cudaMemcpyAsync(dt_host, pl->run_aux + 1, size_t(nsteps) * 8,
+                                      cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess) &&
+         (!status_host || cudaMemcpyAsync(status_host, pl->run_status + G, size_t(G) * 4,
+                                          cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess) &&
+         (!partials_host || cudaMemcpyAsync(partials_host, pl->run_partials, size_t(G) * 48,
+                                            cudaMemcpyDeviceToHost, pl->s_d2h) == cudaSuccess) &&
+         cudaEventRecord(pl->run_end, pl->s_d2h) == cudaSuccess;
+    if (!ok) return GAMER_E_CUDA;
+    pl->d2h_bytes += (dt_host ? 8 * int64_t(nsteps) : 0) + (status_host ? 4 * G : 0) +
+                     (partials_host ? 48 * G : 0);
+    return wait_event(pl->run_end, pl->timeout_s * nsteps);
 }
 
 extern "C" int gamer_pipeline_last_bytes(const gamer_pipeline* pl, int64_t* h2d, int64_t* d2h) {

@@ -126,6 +126,9 @@ def lib():
         L.gamer_pipeline_level_step_host.argtypes = [vp, vp, vp, i32, i32, i32, i32, d, d, vp, vp,
                                                      P(gh_params), i32]
         L.gamer_pipeline_level_step_host.restype = ctypes.c_int
+        L.gamer_pipeline_level_run_host.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, d, d,
+                                                    d, vp, vp, vp, P(gh_params)]
+        L.gamer_pipeline_level_run_host.restype = ctypes.c_int
         L.gamer_pipeline_last_bytes.argtypes = [vp, P(i64), P(i64)]
         L.gamer_pipeline_last_bytes.restype = ctypes.c_int
         L.gamer_pipeline_set_level_mode.argtypes = [vp, i32]
@@ -522,6 +525,26 @@ class Pipeline:
                                                   p(partials), ctypes.byref(params),
                                                   int(nthreads))
         _check(rc, "gamer_pipeline_level_step_host")
+
+    def level_run_host(self, level0, level1, gx, gy, gz, bc, nsteps, dt0, dh, cfl, params,
+                       dt_out=None, status=None, partials=None):
+        """nsteps steps between two host tensors [G,5,16,16,16]: step n reads
+        level[n % 2] and writes level[(n + 1) % 2]; dt0 for step 0, then the
+        CFL dt from the previous step's partials (on the device).  dt_out
+        [nsteps] float64, status [G] int32 (OR over the steps), partials [G,6]
+        float64 (last step): host tensors or None."""
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        for t, nm in ((level0, "level0"), (level1, "level1")):
+            if t.is_cuda or not t.is_contiguous():
+                raise GamerError(-2, f"{nm} must be a contiguous host tensor")
+        for t, nm in ((dt_out, "dt_out"), (status, "status"), (partials, "partials")):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise GamerError(-2, f"{nm} must be a contiguous host tensor")
+        rc = lib().gamer_pipeline_level_run_host(self.handle, p(level0), p(level1), gx, gy, gz, bc,
+                                                 int(nsteps), float(dt0), float(dh), float(cfl),
+                                                 p(dt_out), p(status), p(partials),
+                                                 ctypes.byref(params))
+        _check(rc, "gamer_pipeline_level_run_host")
 
     def set_level_mode(self, mode):
         """0 automatic, 1 device copy of the whole level, 2 slab windows."""

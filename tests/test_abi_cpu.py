@@ -195,6 +195,13 @@ def test_hydro_dt_rejects_bad_arguments(lib):
     assert f(*b) == -3
 
 
+def test_level_run_rejects_a_missing_pipeline(lib):
+    f = lib.gamer_pipeline_level_run_host
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32] * 5 + [ctypes.c_double] * 3 + \
+        [ctypes.c_void_p] * 4
+    assert f(None, None, None, 1, 1, 1, 0, 1, 1e-3, 1.0, 0.5, None, None, None, None) == -1
+
+
 def test_set_launch_shape_validation(lib):
     assert lib.gamer_set_hydro_ctas_per_sm(4, 1) == -2
     assert lib.gamer_set_hydro_ctas_per_sm(0, -1) == -2

@@ -229,3 +229,58 @@ def test_streamed_level_full_size_sampled():
     got = h_out[torch.from_numpy(sample)].double().numpy()
     assert rel_l1_fields(got, r_out) <= TOL_F32_1
     assert np.array_equal(st.numpy()[sample].astype(np.uint32), r_st)
+
+
+@pytest.mark.parametrize("batch", [16, 32, 64], ids=["1-layer", "2-layer", "one-slab"])
+@pytest.mark.parametrize("bc", [0, 1], ids=["periodic", "zero-gradient"])
+@pytest.mark.parametrize("mode", [F32, F64], ids=["f32", "f64"])
+def test_pipeline_level_run_equals_single_steps(mode, bc, batch):
+    """Multi-step run of a host-resident level (slab order rotated every step,
+    the next step's copies in overlapping this step's copies out, dt reduced
+    on the device) against the same steps one call at a time with the dt
+    worked out on the host from the returned partials: the same states, dt
+    sequence, status and partials bit for bit, and the exact byte counts."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g, dh, cfl, nsteps = 5 / 3, 1 / 64, 0.5, 5
+    lv = wl.level_to_groups(wl.fourier_level(n=64, seed=5, gamma=g))
+    T = torch.float64 if mode == F64 else torch.float32
+    G = 64
+    params = native.make_params(g)
+    # reference: one call per step, dt from the previous step's partials
+    ref = native.Pipeline(mode, batch, with_flux=False)
+    ref.set_level_mode(1)
+    a = torch.from_numpy(lv).to(T).pin_memory()
+    b = torch.empty_like(a).pin_memory()
+    st = torch.zeros(G, dtype=torch.int32).pin_memory()
+    part = torch.zeros((G, 6), dtype=torch.float64).pin_memory()
+    ref.level_step_host(a, b, 4, 4, 4, bc, 0.0, dh, st, part, params)   # partials of U^0
+    dt0 = cfl * dh / float(part[:, 0].max())
+    dts, st_or, dt = [], np.zeros(G, dtype=np.uint32), dt0
+    cur, nxt = a.clone().pin_memory(), b
+    for _ in range(nsteps):
+        ref.level_step_host(cur, nxt, 4, 4, 4, bc, dt, dh, st, part, params)
+        dts.append(dt)
+        st_or |= st.numpy().astype(np.uint32)
+        cur, nxt = nxt, cur
+        dt = cfl * dh / float(part[:, 0].max())
+    ref.close()
+    want, want_part = cur.clone(), part.clone()
+    # the run
+    pl = native.Pipeline(mode, batch, with_flux=False)
+    l0 = torch.from_numpy(lv).to(T).pin_memory()
+    l1 = torch.full_like(l0, float("nan")).pin_memory()
+    r_dt = torch.zeros(nsteps, dtype=torch.float64)
+    r_st = torch.zeros(G, dtype=torch.int32)
+    r_part = torch.zeros((G, 6), dtype=torch.float64)
+    pl.level_run_host(l0, l1, 4, 4, 4, bc, nsteps, dt0, dh, cfl, params, r_dt, r_st, r_part)
+    h2d, d2h = pl.last_bytes()
+    pl.close()
+    final = (l0, l1)[nsteps % 2]
+    assert torch.equal(final, want)
+    assert np.array_equal(r_dt.numpy(), np.array(dts))
+    assert np.array_equal(r_st.numpy().astype(np.uint32), st_or)
+    assert torch.equal(r_part, want_part)
+    level_bytes = G * 20480 * (8 if mode == F64 else 4)
+    assert h2d == 16 * G + 16 + nsteps * level_bytes
+    assert d2h == nsteps * level_bytes + 8 * nsteps + 4 * G + 48 * G
