@@ -308,6 +308,87 @@ struct RoeIO {
     T v[5];
     uint32_t st;
 };
+// FP32 Roe solve with the left/right-symmetric work on paired FP32
+// instructions (one instruction, both lanes of a float2: .x the left state,
+// .y the right).  Same formulas as roe_main.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+template <class P>
+__device__ __forceinline__ bool roe_main_x2(const float L[5], const float R[5],
+                                            const KConst<float, P>& kc, float F[5]) {
+    const float2 r = pk(L[0], R[0]), m = pk(L[1], R[1]), ma = pk(L[2], R[2]),
+                 mb = pk(L[3], R[3]), E = pk(L[4], R[4]);
+    const float2 ir = pk(rcp_(L[0]), rcp_(R[0]));
+    const float2 u = __fmul2_rn(m, ir), v = __fmul2_rn(ma, ir), w = __fmul2_rn(mb, ir);
+    const float2 g2 = pk(kc.gm1, kc.gm1), ga2 = pk(kc.gamma, kc.gamma), mh = pk(-0.5f, -0.5f);
+    float2 s = __fmul2_rn(m, m);
+    s = __ffma2_rn(ma, ma, s);
+    s = __ffma2_rn(mb, mb, s);
+    const float2 p = __fmul2_rn(g2, __ffma2_rn(__fmul2_rn(s, ir), mh, E));
+    const float2 Ep = __fadd2_rn(E, p);
+    const float2 H = __fmul2_rn(Ep, ir);
+    const float2 c2 = __fmul2_rn(__fmul2_rn(ga2, p), ir);
+    const float cL = sqrt_(c2.x), cR = sqrt_(c2.y);
+    const float rr = sqrt_(R[0] * ir.x);
+    const float i1 = rcp_(1.0f + rr);
+    const float uT = (u.x + rr * u.y) * i1;
+    const float vT = (v.x + rr * v.y) * i1;
+    const float wT = (w.x + rr * w.y) * i1;
+    const float HT = (H.x + rr * H.y) * i1;
+    const float q2 = uT * uT + vT * vT + wT * wT;
+    const float cT2 = kc.gm1 * (HT - 0.5f * q2);
+    const float cT = sqrt_(cT2);
+    const float rT = rr * L[0];
+    const float dr = R[0] - L[0], du = u.y - u.x, dv = v.y - v.x, dw = w.y - w.x, dp = p.y - p.x;
+    const float ic2 = rcp_(cT2);
+    const float a1 = (dp - rT * cT * du) * (0.5f * ic2);
+    const float a2 = dr - dp * ic2;
+    const float a3 = rT * dv;
+    const float a4 = rT * dw;
+    const float a5 = (dp + rT * cT * du) * (0.5f * ic2);
+    const float K1u = uT - cT, K5u = uT + cT;
+    const float K1E = HT - uT * cT, K5E = HT + uT * cT;
+    // intermediate states U*_L = U_L + a1 K1 (.x), U*_R = U_R - a5 K5 (.y)
+    const float2 A = pk(a1, -a5);
+    const float2 sr = __fadd2_rn(r, A);
+    const float2 sn = __ffma2_rn(A, pk(K1u, K5u), m);
+    const float2 sa = __ffma2_rn(A, pk(vT, vT), ma);
+    const float2 sb = __ffma2_rn(A, pk(wT, wT), mb);
+    const float2 sE = __ffma2_rn(A, pk(K1E, K5E), E);
+    const float2 is = pk(rcp_(sr.x), rcp_(sr.y));
+    float2 ss = __fmul2_rn(sn, sn);
+    ss = __ffma2_rn(sa, sa, ss);
+    ss = __ffma2_rn(sb, sb, ss);
+    const float2 ps = __fmul2_rn(g2, __ffma2_rn(__fmul2_rn(ss, is), mh, sE));
+    const bool fallback =
+        !((cT2 > 0.0f) & (sr.x > 0.0f) & (ps.x > 0.0f) & (sr.y > 0.0f) & (ps.y > 0.0f));
+    const float2 un = __fmul2_rn(sn, is);
+    const float2 cs2 = __fmul2_rn(__fmul2_rn(ga2, ps), is);
+    const float l1s = un.x - sqrt_(cs2.x);
+    const float l5s = un.y + sqrt_(cs2.y);
+    const float d1 = max_(0.0f, max_(K1u - (u.x - cL), l1s - K1u));
+    const float d5 = max_(0.0f, max_(K5u - l5s, (u.y + cR) - K5u));
+    float e1 = abs_(K1u), e5 = abs_(K5u);
+    const float f1 = (K1u * K1u + d1 * d1) * rcp_(2.0f * d1);
+    const float f5 = (K5u * K5u + d5 * d5) * rcp_(2.0f * d5);
+    e1 = (e1 < d1) ? f1 : e1;
+    e5 = (e5 < d5) ? f5 : e5;
+    const float e2 = abs_(uT);
+    const float s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
+    const float D0 = s1 + s2 + s5;
+    const float D1 = s1 * K1u + s2 * uT + s5 * K5u;
+    const float D2 = D0 * vT + s3;
+    const float D3 = D0 * wT + s4;
+    const float D4 = s1 * K1E + s2 * (0.5f * q2) + s3 * vT + s4 * wT + s5 * K5E;
+    const float2 f1n = __ffma2_rn(m, u, p), f2n = __fmul2_rn(m, v), f3n = __fmul2_rn(m, w),
+                 f4n = __fmul2_rn(Ep, u);
+    F[0] = 0.5f * (m.x + m.y) - 0.5f * D0;
+    F[1] = 0.5f * (f1n.x + f1n.y) - 0.5f * D1;
+    F[2] = 0.5f * (f2n.x + f2n.y) - 0.5f * D2;
+    F[3] = 0.5f * (f3n.x + f3n.y) - 0.5f * D3;
+    F[4] = 0.5f * (f4n.x + f4n.y) - 0.5f * D4;
+    return fallback;
+}
+
 template <int MODE, class T, class P>
 __device__ __forceinline__ void hlle_core(const T L[5], const T R[5], const KConst<T, P>& kc,
                                           T F[5]) {
@@ -369,7 +450,10 @@ __device__ __forceinline__ void hlle_apply(const T L[5], const T R[5], const KCo
 template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
                                         T F[5], uint32_t& st) {
-    if (roe_main<MODE>(L, R, kc, F)) hlle_apply<MODE>(L, R, kc, F, st);
+    bool fb;
+    if constexpr (MODE == GAMER_MODE_F32) fb = roe_main_x2(L, R, kc, F);
+    else fb = roe_main<MODE>(L, R, kc, F);
+    if (fb) hlle_apply<MODE>(L, R, kc, F, st);
 }
 
 // Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
