@@ -54,8 +54,8 @@ KERNEL_SOURCES = ["paper_1007_3818_gb300/csrc/hydro_kernel.cuh",
                   "paper_1007_3818_gb300/csrc/device_util.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_launch.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_f32.cu"]
-NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "ctas_per_sm": 3, "bytes": 779163648,
-               "sources_sha256": "9a471fd7ae63b69aa8f6f13ab91f006082b480dbd4a34ff82fb6c5e9749033f8"}
+NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "ctas_per_sm": 3, "bytes": 771799040,
+               "sources_sha256": "20d24059d7bb820bdea07c799a4c7553d0749f1d3f4eff3084392279ad0fa382"}
 
 
 def kernel_sources_sha256():
@@ -275,10 +275,12 @@ def streamed_main(args):
     pl.level_step_host(lv[0], lv[1], gx, gx, gx, 0, 0.0, dh, st, part, params)
     dt0 = CFL * dh / float(part[:, 0].max())              # FP64 reduction of the partials
     dts = torch.zeros(args.steps, dtype=torch.float64, pin_memory=True)
-    pl.level_run_host(lv[0], lv[1], gx, gx, gx, 0, 1, dt0, dh, CFL, params)  # allocation
+    # the clock sampler starts before the allocating call, so that its own
+    # start-up is over before the timed region
     clocks = ClockSampler(0)
     clocks.start()
-    time.sleep(0.3)
+    pl.level_run_host(lv[0], lv[1], gx, gx, gx, 0, 1, dt0, dh, CFL, params)  # allocation
+    time.sleep(1.0)
     t0 = time.perf_counter()
     torch.cuda.nvtx.range_push("streamed level run")
     pl.level_run_host(lv[0], lv[1], gx, gx, gx, 0, args.steps, dt0, dh, CFL, params, dts, st,
