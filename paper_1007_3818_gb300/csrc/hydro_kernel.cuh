@@ -684,7 +684,7 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
         const T* lo = (d == 2) ? Wm + c : W0 + c - (d == 0 ? 1 : 20);
         const T* hi = (d == 2) ? Wp + c : W0 + c + (d == 0 ? 1 : 20);
         T wm[5], wp[5];
-        if constexpr (MODE == GAMER_MODE_F32 && LIM == 0 && REC == 0) {
+        if constexpr (sizeof(T) == 4 && LIM == 0 && REC == 0) {  // every FP32-storage mode
             faces_vanleer_x2(lo, wc, hi, kc, wm, wp);
         } else {
             T sl[5];

@@ -126,14 +126,17 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         }
     }
     if (special) {
-        // Riemann solver in bits 0-1, characteristic limiting in bit 2
-        const int rsv = (hllc ? 2 : 0) | (chr ? 4 : 0);
+        // Riemann solver in bits 0-1, characteristic limiting in bit 2; HLLC
+        // with the van Leer limiter also has it compiled in (bit 3)
+        const int rsv = (hllc ? 2 : 0) | (chr ? 4 : 0) | ((hllc && !chr && vl) ? 8 : 0);
         if constexpr (MODE == GAMER_MODE_F64) {
-            kern = rsv == 2   ? hydro_step_kernel<MODE, 1, 2, SRC, 3>
+            kern = rsv == 10  ? hydro_step_kernel<MODE, 1, 10, SRC, 3>
+                   : rsv == 2 ? hydro_step_kernel<MODE, 1, 2, SRC, 3>
                    : rsv == 4 ? hydro_step_kernel<MODE, 1, 4, SRC, 3>
                               : hydro_step_kernel<MODE, 1, 6, SRC, 3>;
         } else {
-            kern = rsv == 2   ? hydro_step_kernel<MODE, 3, 2, SRC, 2>
+            kern = rsv == 10  ? hydro_step_kernel<MODE, 3, 10, SRC, 2>
+                   : rsv == 2 ? hydro_step_kernel<MODE, 3, 2, SRC, 2>
                    : rsv == 4 ? hydro_step_kernel<MODE, 3, 4, SRC, 2>
                               : hydro_step_kernel<MODE, 3, 6, SRC, 2>;
             smem = int(sizeof(Smem<T, 2>)) + extra;
