@@ -308,22 +308,34 @@ struct RoeIO {
     T v[5];
     uint32_t st;
 };
-// FP32 Roe solve with the left/right-symmetric work on paired FP32
-// instructions (one instruction, both lanes of a float2: .x the left state,
-// .y the right).  Same formulas as roe_main.
+// Roe solve of the FP32-storage modes with the left/right-symmetric work on
+// paired FP32 instructions (one instruction, both lanes of a float2: .x the
+// left state, .y the right).  Same formulas as roe_main; the FP32 mode also
+// pairs its pressure recoveries, the mixed and float-float modes recover each
+// lane's pressure in their own precision.
 __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
-template <class P>
+template <int MODE, class P>
+__device__ __forceinline__ float2 pressure_x2(float2 r, float2 m, float2 ma, float2 mb, float2 E,
+                                              float2 ir, const KConst<float, P>& kc) {
+    if constexpr (MODE == GAMER_MODE_F32) {
+        float2 s = __fmul2_rn(m, m);
+        s = __ffma2_rn(ma, ma, s);
+        s = __ffma2_rn(mb, mb, s);
+        return __fmul2_rn(pk(kc.gm1, kc.gm1), __ffma2_rn(__fmul2_rn(s, ir), pk(-0.5f, -0.5f), E));
+    } else {
+        return pk(pressure<MODE>(r.x, m.x, ma.x, mb.x, E.x, ir.x, kc),
+                  pressure<MODE>(r.y, m.y, ma.y, mb.y, E.y, ir.y, kc));
+    }
+}
+template <int MODE, class P>
 __device__ __forceinline__ bool roe_main_x2(const float L[5], const float R[5],
                                             const KConst<float, P>& kc, float F[5]) {
     const float2 r = pk(L[0], R[0]), m = pk(L[1], R[1]), ma = pk(L[2], R[2]),
                  mb = pk(L[3], R[3]), E = pk(L[4], R[4]);
     const float2 ir = pk(rcp_(L[0]), rcp_(R[0]));
     const float2 u = __fmul2_rn(m, ir), v = __fmul2_rn(ma, ir), w = __fmul2_rn(mb, ir);
-    const float2 g2 = pk(kc.gm1, kc.gm1), ga2 = pk(kc.gamma, kc.gamma), mh = pk(-0.5f, -0.5f);
-    float2 s = __fmul2_rn(m, m);
-    s = __ffma2_rn(ma, ma, s);
-    s = __ffma2_rn(mb, mb, s);
-    const float2 p = __fmul2_rn(g2, __ffma2_rn(__fmul2_rn(s, ir), mh, E));
+    const float2 ga2 = pk(kc.gamma, kc.gamma);
+    const float2 p = pressure_x2<MODE>(r, m, ma, mb, E, ir, kc);
     const float2 Ep = __fadd2_rn(E, p);
     const float2 H = __fmul2_rn(Ep, ir);
     const float2 c2 = __fmul2_rn(__fmul2_rn(ga2, p), ir);
@@ -355,10 +367,7 @@ __device__ __forceinline__ bool roe_main_x2(const float L[5], const float R[5],
     const float2 sb = __ffma2_rn(A, pk(wT, wT), mb);
     const float2 sE = __ffma2_rn(A, pk(K1E, K5E), E);
     const float2 is = pk(rcp_(sr.x), rcp_(sr.y));
-    float2 ss = __fmul2_rn(sn, sn);
-    ss = __ffma2_rn(sa, sa, ss);
-    ss = __ffma2_rn(sb, sb, ss);
-    const float2 ps = __fmul2_rn(g2, __ffma2_rn(__fmul2_rn(ss, is), mh, sE));
+    const float2 ps = pressure_x2<MODE>(sr, sn, sa, sb, sE, is, kc);
     const bool fallback =
         !((cT2 > 0.0f) & (sr.x > 0.0f) & (ps.x > 0.0f) & (sr.y > 0.0f) & (ps.y > 0.0f));
     const float2 un = __fmul2_rn(sn, is);
@@ -451,7 +460,7 @@ template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
                                         T F[5], uint32_t& st) {
     bool fb;
-    if constexpr (MODE == GAMER_MODE_F32) fb = roe_main_x2(L, R, kc, F);
+    if constexpr (sizeof(T) == 4) fb = roe_main_x2<MODE>(L, R, kc, F);  // FP32 storage
     else fb = roe_main<MODE>(L, R, kc, F);
     if (fb) hlle_apply<MODE>(L, R, kc, F, st);
 }

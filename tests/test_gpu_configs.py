@@ -284,3 +284,36 @@ def test_pipeline_level_run_equals_single_steps(mode, bc, batch):
     level_bytes = G * 20480 * (8 if mode == F64 else 4)
     assert h2d == 16 * G + 16 + nsteps * level_bytes
     assert d2h == nsteps * level_bytes + 8 * nsteps + 4 * G + 48 * G
+
+
+@pytest.mark.parametrize("mode", [F32, F64], ids=["f32", "f64"])
+def test_pipeline_level_run_edge_cases(mode):
+    """nsteps 0 touches nothing; dt0 = 0 leaves the state bitwise unchanged;
+    one step equals one level_step_host call bit for bit."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g, dh, cfl = 1.4, 1 / 64, 0.4
+    lv = wl.level_to_groups(wl.fourier_level(n=64, seed=6, gamma=g))
+    T = torch.float64 if mode == F64 else torch.float32
+    G, params = 64, native.make_params(g)
+    pl = native.Pipeline(mode, 32, with_flux=False)
+    l0 = torch.from_numpy(lv).to(T).pin_memory()
+    l1 = torch.full_like(l0, float("nan")).pin_memory()
+    pl.level_run_host(l0, l1, 4, 4, 4, 1, 0, 1e-3, dh, cfl, params)
+    assert pl.last_bytes() == (0, 0) and torch.isnan(l1).all()
+    r_dt = torch.full((1,), -1.0, dtype=torch.float64)
+    r_st = torch.full((G,), -1, dtype=torch.int32)
+    r_part = torch.zeros((G, 6), dtype=torch.float64)
+    pl.level_run_host(l0, l1, 4, 4, 4, 1, 1, 0.0, dh, cfl, params, r_dt, r_st, r_part)
+    assert torch.equal(l1, l0) and float(r_dt[0]) == 0.0 and (r_st == 0).all()
+    dt = cfl * dh / float(r_part[:, 0].max())
+    pl.level_run_host(l0, l1, 4, 4, 4, 1, 1, dt, dh, cfl, params, r_dt, r_st, r_part)
+    pl.close()
+    ref = native.Pipeline(mode, 32, with_flux=False)
+    out = torch.empty_like(l0).pin_memory()
+    st = torch.zeros(G, dtype=torch.int32).pin_memory()
+    part = torch.zeros((G, 6), dtype=torch.float64).pin_memory()
+    ref.level_step_host(l0, out, 4, 4, 4, 1, dt, dh, st, part, params)
+    ref.close()
+    assert torch.equal(l1, out) and torch.equal(r_part, part) and torch.equal(r_st, st)
+    assert float(r_dt[0]) == dt
