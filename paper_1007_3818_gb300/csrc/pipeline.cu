@@ -841,16 +841,16 @@ extern "C" int gamer_pipeline_level_run_host(gamer_pipeline* pl, void* level0, v
                                 pl->run_dt + g0, pl->run_dt + G + g0, pl->run_status + g0,
                                 pl->run_partials + g0 * 6, p);
             if (rc != GAMER_OK) return rc;
-            BufSet& S = pl->set[i % kSets];
-            ok = cudaEventRecord(S.comp_done, pl->s_comp) == cudaSuccess &&
-                 cudaStreamWaitEvent(pl->s_d2h, S.comp_done, 0) == cudaSuccess &&
+            // the slab's kernel -> its copy out (only the set's event is used)
+            const cudaEvent_t done = pl->set[i % kSets].comp_done;
+            ok = cudaEventRecord(done, pl->s_comp) == cudaSuccess &&
+                 cudaStreamWaitEvent(pl->s_d2h, done, 0) == cudaSuccess &&
                  cudaMemcpyAsync(hout + size_t(z0) * layer_bytes, dout + size_t(z0) * layer_bytes,
                                  size_t(nz) * layer_bytes, cudaMemcpyDeviceToHost,
                                  pl->s_d2h) == cudaSuccess &&
                  cudaEventRecord(ev_out[s], pl->s_d2h) == cudaSuccess;
             if (!ok) return GAMER_E_CUDA;
             pl->d2h_bytes += ng * 20480 * int64_t(e);
-            S.used = true;
         }
         status_or_kernel<<<or_blocks, 256, 0, pl->s_comp>>>(pl->run_status + G, pl->run_status,
                                                            G);
