@@ -13,12 +13,18 @@ Method (paper Sec. 2): MUSCL-Hancock (Toro 2009) with Roe's Riemann solver
 solver, full-step update); five-point stencil per direction.  The readings
 taken where the paper is silent are listed at the top of ``gamer_oracle.cpp``.
 
-Pins (tests/test_oracle_*.py): exact Riemann star values for Sod (textbook),
-Rankine-Hugoniot and Riemann-invariant residuals, Roe's exactness on isolated
-shocks and stationary contacts, HLLE limits, limiter closed forms, exact
-preservation of uniform states, conservation on periodic boxes, permutation
-and mirror symmetry, L1 convergence on Sod / Lax, second-order convergence on
-a linear sound wave, ghost-independence of unread corner cells.
+Pins (tests/test_oracle_pins.py, test_hllc_oracle.py, test_char_oracle.py,
+test_amr_oracle.py, test_host_fill_cpu.py): exact Riemann star values for Sod
+(textbook), Rankine-Hugoniot and Riemann-invariant residuals, Roe's exactness
+on isolated shocks and stationary contacts, HLLE limits, limiter closed forms,
+exact preservation of uniform states, conservation on periodic boxes,
+permutation and mirror symmetry, L1 convergence on Sod / Lax, second-order
+convergence on a linear sound wave, ghost-independence of unread corner cells;
+the floors' closed forms; HLLC's exactness on isolated contact and shear
+waves, upwinding and consistency; characteristic limiting reducing to the
+primitive scheme on an entropy wave and limiting single waves along their
+eigenvectors; composite conservation, locality and exact means of the
+coarse-fine fix-up and restriction; the ghost fill against index arithmetic.
 """
 from __future__ import annotations
 
