@@ -214,3 +214,26 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(native, "LIB_PATH", "/nonexistent/libgamer_gb300.so")
     with pytest.raises(native.GamerError):
         native.lib()
+
+
+def test_level_run_binding_checks_tensors_before_the_call(lib):
+    """The binding rejects a non-contiguous host level before any C call, and
+    a pipeline without a handle (NULL) gets GAMER_E_NULL from the library --
+    no device is touched on either path."""
+    torch = pytest.importorskip("torch")
+    pl = native.Pipeline.__new__(native.Pipeline)
+    pl.handle = None
+    pl.mode = native.GAMER_MODE_F32
+    good = torch.zeros((1, 5, 16, 16, 16), dtype=torch.float32)
+    strided = torch.zeros((1, 5, 16, 16, 32), dtype=torch.float32)[..., ::2]
+    params = native.make_params(1.4)
+    with pytest.raises(native.GamerError) as e:
+        pl.level_run_host(strided, good, 1, 1, 1, 0, 1, 1e-3, 1.0, 0.5, params)
+    assert e.value.code == -2
+    with pytest.raises(native.GamerError) as e:
+        pl.level_run_host(good, good.clone(), 1, 1, 1, 0, 1, 1e-3, 1.0, 0.5, params,
+                          dt_out=torch.zeros(4, dtype=torch.float64)[::2])
+    assert e.value.code == -2
+    with pytest.raises(native.GamerError) as e:
+        pl.level_run_host(good, good.clone(), 1, 1, 1, 0, 1, 1e-3, 1.0, 0.5, params)
+    assert e.value.code == -1
