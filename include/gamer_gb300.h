@@ -52,7 +52,10 @@ extern "C" {
 #define GAMER_ST_HLLE_FALLBACK      0x2u /* a face used HLLE instead of Roe                       */
 #define GAMER_ST_NONPOSITIVE_OUT    0x4u /* an updated cell has rho <= 0 or p <= 0 (or NaN)       */
 #define GAMER_ST_BAD_INPUT          0x8u /* non-finite read input, or dt < 0 / dh <= 0 / non-finite */
-#define GAMER_ST_INTERNAL_TIMEOUT  0x10u /* a bounded on-chip wait gave up; outputs are invalid  */
+#define GAMER_ST_INTERNAL_TIMEOUT  0x10u /* a bounded on-chip wait gave up; outputs are invalid:
+                                            the CTA stops, so this group and every later
+                                            group it owned carry the bit, get NaN partials
+                                            and keep whatever out / face_flux held        */
 #define GAMER_ST_FLOOR             0x20u /* a density or pressure floor changed an updated cell   */
 
 /* ---- precision modes ---- */
@@ -231,6 +234,8 @@ int gamer_fill_ghosts_uniform_f64(const double* level, double* in, int32_t gx, i
  *                 (0 when no group of level l has a positive signal speed)
  *   totals[5]   = sum over all groups of partials[g][1..5]      (may be NULL)
  *   dt_group[g] = dt_out[level[g]], the next step's dt per group (may be NULL)
+ * A NaN speed in the partials (a group the step abandoned, see
+ * GAMER_ST_INTERNAL_TIMEOUT) makes its level's dt NaN.
  * level [N] int32 in [0, n_levels) or NULL (all groups in level 0);
  * 1 <= n_levels <= 64; cfl finite and > 0.  dh_level [n_levels], dt_out
  * [n_levels], totals [5], dt_group [N] are device arrays.  The reduction is
@@ -255,9 +260,11 @@ int gamer_hydro_dt(const double* partials, int64_t N, const int32_t* level, int3
  * gamer_hydro_dt_workspace_bytes(N, n_levels), fits in 64 KiB -- every N up to
  * 64 Ki groups, and every N for n_levels <= 3 -- and returns GAMER_E_WORKSPACE
  * for larger ones.  Arguments, results and other errors are those of
- * gamer_hydro_dt.  The first call on a device looks up the scratch array's
- * device address (with that device current); make that first call before
- * any stream capture.  All calls share the one array and every call rewrites
+ * gamer_hydro_dt.  The call looks up the scratch array's device address
+ * (with the device current) every time it is made outside stream capture, so
+ * it keeps working after cudaDeviceReset; during a capture it uses the address
+ * of its last lookup on that device, so make the first call on a device
+ * before any stream capture.  All calls share the one array and every call rewrites
  * the part it reads, so nothing needs clearing between calls; calls whose GPU
  * work overlaps (different streams, no ordering between them) race on it.
  */
@@ -308,6 +315,15 @@ int gamer_level_graph_destroy(gamer_level_graph* g);
  * (gamer_pipeline_set_timeout, default 60 s) and returns GAMER_E_TIMEOUT if
  * the GPU has not finished by then.  It allocates nothing.  One pipeline must
  * not be used by two host threads at once.
+ *
+ * After GAMER_E_TIMEOUT (here or in any gamer_pipeline_* call that copies),
+ * that call's copies may still be queued: they will still read its host
+ * inputs and write its host outputs.  Keep those buffers alive and untouched
+ * until a later call on the pipeline returns GAMER_OK or
+ * gamer_pipeline_destroy returns (it waits for the pipeline's streams).  Every
+ * call on a pipeline whose previous call timed out first waits, up to the
+ * timeout, for the pipeline's streams to drain, and returns GAMER_E_TIMEOUT
+ * again, with nothing enqueued, if they have not.
  */
 typedef struct gamer_pipeline gamer_pipeline;
 int gamer_pipeline_create(int32_t mode, int64_t batch_groups, int32_t with_flux,
@@ -317,6 +333,10 @@ int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_host, void* o
                                 const double* dh_host, uint32_t* status_host,
                                 double* partials_host, int64_t N, const gh_params* p);
 int gamer_pipeline_set_timeout(gamer_pipeline* pl, double seconds);
+/* Test facility (not part of the scheme): holds the pipeline's three streams
+ * for `seconds` (0 .. 60) with a host callback that sleeps, so that the next
+ * call's bounded wait can be made to run out without any GPU-side wait. */
+int gamer_pipeline_debug_hold(gamer_pipeline* pl, double seconds);
 
 /*
  * gamer_pipeline_level_step_host: one step of a uniform level that lives in
@@ -413,15 +433,17 @@ const char* gamer_version(void);
  * SM of the persistent grid.  The FP32 modes come in two builds, sized for 2
  * CTAs per SM (no register spills) and for 3 (more warps per SM); 2 selects
  * the first, 0 or 3 the second (default).  FP64 always runs 1 CTA per SM.
- * Larger values are capped at what fits.  Used by the autotuner;
- * process-wide setting. */
+ * Larger values are capped at what fits.  Used by the autotuner.
+ * Process-wide and unsynchronised: every later launch of any host thread
+ * reads it, so change it only while no other thread is launching steps. */
 int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
 
 /* Code shape of the hydro kernel: 0 = one problem at a time per thread
  * (default); 1 = as 0 with one out-of-line copy of the Riemann solver (FP32
  * 3-CTA build only); 2 = two interleaved problems per thread (z-face states in
  * shared memory, branch-free Roe path, compile-time limiter; 2 CTAs per SM in
- * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide setting. */
+ * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide and
+ * unsynchronised like gamer_set_hydro_ctas_per_sm. */
 int gamer_set_hydro_variant(int32_t variant);
 
 /* Debug facility (not part of the scheme): with on = 1, every later launch of
@@ -432,6 +454,17 @@ int gamer_set_hydro_variant(int32_t variant);
  * covers every cell read.  Process-wide; 0 (default) turns it off.  Returns
  * GAMER_E_PARAM for other values. */
 int gamer_set_debug_poison(int32_t on);
+
+/* Failure-detection test facility (not part of the scheme): with group >= 0,
+ * every later launch of gamer_hydro_advance_* (default code shape) and of the
+ * level kernels never issues the copy of input plane 5 of that group, so the
+ * CTA's bounded wait for it runs out and its give-up path runs
+ * (GAMER_ST_INTERNAL_TIMEOUT, see there) -- no fault, no hang.  wait_polls > 0
+ * bounds every on-chip wait of those launches to that many polls (0: the
+ * default bound, about 4 million).  group = -1 and wait_polls = 0 restore
+ * normal operation.  Process-wide and unsynchronised; GAMER_E_PARAM for group
+ * < -1 or wait_polls < 0. */
+int gamer_set_debug_drop_plane(int64_t group, int32_t wait_polls);
 
 /*
  * AMR coarse-fine coupling after one coarse step and its fine sub-steps: the

@@ -98,6 +98,7 @@ def _load():
         lib.oracle_exact_riemann_star.argtypes = [d, d, d, d, d, d, d, pd]
         lib.oracle_exact_riemann_sample.argtypes = [d, d, d, d, d, d, d, d, pd]
         lib.oracle_count_ops_group.argtypes = [pd, d, d, P(_Params), pd]
+        lib.oracle_count_ops_piece.argtypes = [ctypes.c_int, ctypes.c_int, pd, pd, d, pd]
         vp = ctypes.c_void_p
         lib.oracle_flux_fixup.argtypes = [pd, pd, pd, ctypes.c_int, pd, pd, i64, i64, vp, i64]
         lib.oracle_flux_fixup.restype = i64
@@ -105,7 +106,7 @@ def _load():
         lib.oracle_restrict.restype = i64
         for name in ("oracle_advance_box", "oracle_advance_groups", "oracle_fill_ghosts_uniform",
                      "oracle_hydro_dt", "oracle_roe_flux", "oracle_exact_riemann_star",
-                     "oracle_count_ops_group"):
+                     "oracle_count_ops_group", "oracle_count_ops_piece"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -336,3 +337,20 @@ def count_ops_group(U_in_group, dt, dh, gamma=5.0 / 3.0, limiter=0, predictor_fa
     if rc != 0:
         raise ValueError("oracle_count_ops_group rejected its arguments")
     return dict(zip(("add", "mul", "div", "sqrt", "cmp", "cells"), c.tolist()))
+
+
+PIECES = {"prim": 0, "cons": 1, "flux": 2, "limiter": 3, "roe": 4, "positive": 5}
+
+
+def count_ops_piece(piece, a, b=None, gamma=5.0 / 3.0, d=0):
+    """Operation tally of one scheme piece (see PIECES) on the counting scalar:
+    dict of add, mul, div, sqrt, cmp.  a, b: length-5 arrays (the limiter and
+    the flux read a[0], b[0] / a, b[0])."""
+    A = _f64(np.resize(np.asarray(a, dtype=np.float64), 5))
+    B = None if b is None else _f64(np.resize(np.asarray(b, dtype=np.float64), 5))
+    c = np.empty(5)
+    rc = _load().oracle_count_ops_piece(PIECES[piece], int(d), _ptr(A), _ptr(B), float(gamma),
+                                        _ptr(c))
+    if rc != 0:
+        raise ValueError("oracle_count_ops_piece rejected its arguments")
+    return dict(zip(("add", "mul", "div", "sqrt", "cmp"), c.tolist()))

@@ -840,6 +840,37 @@ void oracle_exact_riemann_sample(double rl, double ul, double pl, double rr, dou
     W[2] = o_p;
 }
 
+int oracle_count_ops_piece(int piece, int dir, const double* a, const double* b, double gamma,
+                           double counts[5]) {
+    if (!a || !counts || piece < 0 || piece > 5 || dir < 0 || dir > 2 ||
+        !(std::isfinite(gamma) && gamma > 1.0))
+        return -1;
+    if ((piece == 2 || piece == 3 || piece == 4) && !b) return -1;
+    oracle_params p = {};
+    p.gamma = gamma;
+    Scheme<Cnt> S = make_scheme<Cnt>(&p);
+    Cnt A[5], B[5], R[5];
+    for (int q = 0; q < 5; ++q) {
+        A[q] = Cnt(a[q]);
+        B[q] = Cnt(b ? b[q] : 0.0);
+    }
+    g_tally = Tally();
+    switch (piece) {
+        case 0: S.prim(A, R); break;
+        case 1: S.cons(A, R); break;
+        case 2: Scheme<Cnt>::flux(dir, A, B[0], R); break;
+        case 3: R[0] = S.limit(A[0], B[0]); break;
+        case 4: S.roe(dir, A, B, true, R); break;
+        default: (void)S.positive(A); break;
+    }
+    counts[0] = g_tally.add;
+    counts[1] = g_tally.mul;
+    counts[2] = g_tally.div;
+    counts[3] = g_tally.sqrt;
+    counts[4] = g_tally.cmp;
+    return 0;
+}
+
 int oracle_count_ops_group(const double* in, double dt, double dh, const oracle_params* p,
                            double counts[6]) {
     if (!in || !counts || !params_ok(p)) return -1;

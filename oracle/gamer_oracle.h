@@ -153,6 +153,16 @@ void oracle_exact_riemann_sample(double rl, double ul, double pl, double rr, dou
 int oracle_count_ops_group(const double* in, double dt, double dh, const oracle_params* p,
                            double counts[6]);
 
+/* Operation tally of one piece of the scheme on the counting scalar, for pins
+ * of the tally against hand counts: piece 0 prim(a), 1 cons(a), 2 the Euler
+ * flux along dir of primitive a with total energy b[0], 3 the configured
+ * (default van Leer) limiter of a[0], b[0], 4 one Roe flux along dir of the
+ * conserved states a, b (entropy fix on), 5 the admissibility test of the
+ * conserved state a.  counts[5] = {add/sub, mul, div, sqrt, compare}.
+ * Returns 0, or -1 on a bad argument. */
+int oracle_count_ops_piece(int piece, int dir, const double* a, const double* b, double gamma,
+                           double counts[5]);
+
 #ifdef __cplusplus
 }
 #endif

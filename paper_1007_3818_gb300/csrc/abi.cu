@@ -43,6 +43,16 @@ int& hydro_debug_poison() {
     return v;
 }
 
+int64_t& hydro_debug_drop_group() {
+    static int64_t v = -1;
+    return v;
+}
+
+uint32_t& hydro_debug_wait_polls() {
+    static uint32_t v = 0;
+    return v;
+}
+
 int& hydro_variant() {
     static int v = 0;
     return v;
@@ -91,5 +101,12 @@ extern "C" int gamer_set_hydro_variant(int32_t variant) {
 extern "C" int gamer_set_debug_poison(int32_t on) {
     if (on != 0 && on != 1) return GAMER_E_PARAM;
     gamer::hydro_debug_poison() = on;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_set_debug_drop_plane(int64_t group, int32_t wait_polls) {
+    if (group < -1 || wait_polls < 0) return GAMER_E_PARAM;
+    gamer::hydro_debug_drop_group() = group;
+    gamer::hydro_debug_wait_polls() = uint32_t(wait_polls);
     return GAMER_OK;
 }

@@ -836,6 +836,11 @@ struct LevelGeom {
     int gx, gy, gz, bc;
     int zb, z0;
     int poison;  // debug: fill each input slot with NaN before gathering into it
+    // debug: the copy of input plane 5 of group drop_group (-1: none) is never
+    // issued, so the wait for it runs out (after wait_polls polls) and the
+    // give-up path runs; wait_polls 0 means the default kWaitPolls
+    int64_t drop_group;
+    uint32_t wait_polls;
 };
 
 // Level coordinate X, at most two cells outside [0, n), mapped into the level:
@@ -972,10 +977,15 @@ template <int SRC, int RING, class T> struct PlaneLoader;
 template <int RING, class T> struct PlaneLoader<0, RING, T> {
     static constexpr size_t kExtraSmem = 0;
     const T* gin;
-    __device__ __forceinline__ PlaneLoader(const T* in, int64_t g, const LevelGeom&, GatherPlan*)
-        : gin(in + g * 40000) {}
-    template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {
+    bool drop;  // debug: withhold plane 5 (LevelGeom::drop_group)
+    __device__ __forceinline__ PlaneLoader(const T* in, int64_t g, const LevelGeom& geo,
+                                           GatherPlan*)
+        : gin(in + g * 40000), drop(g == geo.drop_group) {}
+    // true when the copy was issued (always, but for the debug drop)
+    template <class SM> __device__ __forceinline__ bool load(SM& S, int kp) const {
+        if (drop && kp == 5) return false;
         if (threadIdx.x == 0) issue_plane<RING>(S, gin, kp);
+        return true;
     }
 };
 template <int RING, class T> struct PlaneLoader<1, RING, T> {
@@ -984,14 +994,16 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
     const LevelGeom& L;
     GatherPlan* plan;
     int bz;
+    bool drop;  // debug: withhold plane 5 (LevelGeom::drop_group)
     __device__ __forceinline__ PlaneLoader(const T* in, int64_t g, const LevelGeom& geo,
                                            GatherPlan* plan_)
-        : level(in), L(geo), plan(plan_ + threadIdx.x) {
+        : level(in), L(geo), plan(plan_ + threadIdx.x), drop(g == geo.drop_group) {
         const int bx = int(g % geo.gx), by = int((g / geo.gx) % geo.gy);
         bz = geo.z0 + int(g / (int64_t(geo.gx) * geo.gy));
         *plan = make_plan<T>(geo, bx, by);  // read back by this thread only
     }
-    template <class SM> __device__ __forceinline__ void load(SM& S, int kp) const {
+    template <class SM> __device__ __forceinline__ bool load(SM& S, int kp) const {
+        if (drop && kp == 5) return false;  // debug: no copy, no arrival
         if (L.poison) {
             // debug: cells the gather does not write read back as NaN, so a
             // stencil read outside the gathered set shows up in the results
@@ -1003,6 +1015,7 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
         }
         const GatherPlan P = *plan;
         gather_plane<RING>(S, level, L, P, bz, kp);
+        return true;
     }
 };
 
@@ -1026,6 +1039,22 @@ template <> struct SumAcc<float> {
     }
     __device__ __forceinline__ double get(int q) const { return double(hi[q]) + double(lo[q]); }
 };
+
+// A bounded on-chip wait of this CTA gave up in group g, so the CTA stops:
+// every group it still owns (g, g + gridDim.x, ...) is marked
+// GAMER_ST_INTERNAL_TIMEOUT and gets NaN partials, which gamer_hydro_dt turns
+// into a NaN time step for the group's level -- the failure shows even when
+// the caller passed no status array.  Their out and face-flux values are left
+// as they were.  Called by one thread.
+__device__ __forceinline__ void mark_abandoned(int64_t g, int64_t N, uint32_t* status,
+                                               double* partials) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t h = g; h < N; h += gridDim.x) {
+        if (status) status[h] = GAMER_ST_INTERNAL_TIMEOUT;
+        if (partials)
+            for (int q = 0; q < 6; ++q) partials[h * 6 + q] = nan;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // MINB: CTAs per SM the register budget is sized for (launch bounds); the
@@ -1055,6 +1084,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     constexpr int ROFF = raw_offset<SRC, T>();
     GatherPlan* gplan = reinterpret_cast<GatherPlan*>(smem_bytes + sizeof(Smem<T, RING>));
     const uint32_t rmask = read_cell_mask();
+    const uint32_t polls = geo.wait_polls ? geo.wait_polls : kWaitPolls;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
@@ -1096,7 +1126,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
         // one input plane into its ring slot (all threads call load_plane)
         const PlaneLoader<SRC, RING, T> loader(in, g, geo, gplan);
-        auto load_plane = [&](int kp) { loader.load(S, kp); };
+        auto load_plane = [&](int kp) { return loader.load(S, kp); };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * (kc.flux9 ? 9 : 6) * kFluxPlane : nullptr;
         const double dtg = dt[g], dhg = dh[g];
@@ -1116,7 +1146,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         load_plane(-1);
         if (RING == 3) load_plane(0);
         pending |= (RING == 3) ? 7u : 3u;
-        if (mbar_wait(&S.mbar[0], parity & 1u)) {
+        if (mbar_wait(&S.mbar[0], parity & 1u, polls)) {
             parity ^= 1u;
             pending &= ~1u;
             convert_plane<MODE>(S.raw[0] + ROFF, S.W[0], plane_read_bits(rmask, -2), kc, st);
@@ -1128,7 +1158,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         pending |= 1u;
         for (int kp = -1; kp <= 0; ++kp) {
             const int s = (kp + 2) % RING;
-            if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u)) {
+            if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u, polls)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
                 convert_plane<MODE>(S.raw[s] + ROFF, S.W[kp + 2], plane_read_bits(rmask, kp), kc,
@@ -1255,8 +1285,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 __syncthreads();
                 // plane k has been read: its slot takes plane k + RING
                 if (k + RING <= 17) {
-                    load_plane(k + RING);
-                    pending |= 1u << ((k + 2) % RING);
+                    if (load_plane(k + RING)) pending |= 1u << ((k + 2) % RING);
                 }
 
                 // ---- phase B(k): Riemann solves
@@ -1360,7 +1389,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 // plane k+2 -> primitives (into the slot of plane k-1)
                 if (k <= 15) {
                     const int slot = (k + 4) % RING;
-                    if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u)) {
+                    if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u, polls)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
                         convert_plane<MODE>(S.raw[slot] + ROFF, S.W[(k + 4) % 3],
@@ -1412,12 +1441,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
     abort_group:
         // A bulk copy did not complete in time.  Wait (bounded) for every copy
-        // still in flight so none lands after the CTA exits, flag the group and
-        // stop this CTA.
+        // still in flight so none lands after the CTA exits, flag this group
+        // and every later one of the CTA, and stop.
         if (tid == 0) {
             for (int s = 0; s < RING; ++s)
                 if (pending & (1u << s)) mbar_wait(&S.mbar[s], (parity >> s) & 1u);
-            if (status) status[g] = GAMER_ST_INTERNAL_TIMEOUT;
+            mark_abandoned(g, N, status, partials);
         }
         return;
     }

@@ -13,6 +13,10 @@ int& hydro_ctas_per_sm_override(int mode);
 // out-of-line copy); chosen by the autotuner.
 int& hydro_variant();
 int& hydro_debug_poison();
+// debug: group whose plane-5 copy is withheld (-1: none) and the poll limit
+// of the on-chip waits (0: default)
+int64_t& hydro_debug_drop_group();
+uint32_t& hydro_debug_wait_polls();
 
 // Common launch path.  SRC 0: `in` = N tiles [N][5][20]^3; SRC 1: `in` = the
 // level `geo` (N = gx*gy*gz), ghosts gathered in the kernel.
@@ -173,7 +177,8 @@ int hydro_advance(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                   typename Prec<MODE>::T* face_flux, const double* dt, const double* dh,
                   uint32_t* status, double* partials, int64_t N, const gh_params* p,
                   void* stream) {
-    const LevelGeom geo = {1, 1, 1, 0, 0, 0, 0};
+    const LevelGeom geo = {1, 1, 1, 0, 0, 0, 0, hydro_debug_drop_group(),
+                           hydro_debug_wait_polls()};
     return hydro_launch<MODE, 0>(in, out, face_flux, dt, dh, status, partials, N, p, geo,
                                  stream);
 }
@@ -190,7 +195,8 @@ int hydro_advance_level(const typename Prec<MODE>::T* level, typename Prec<MODE>
     // the gather's per-group plan holds level offsets within a z-layer of
     // groups in units of 16 cells as 32-bit integers
     if (int64_t(gx) * gy * 1280 + 2048 > INT32_MAX) return GAMER_E_PARAM;
-    const LevelGeom geo = {gx, gy, gz, bc, 0, 0, hydro_debug_poison()};
+    const LevelGeom geo = {gx, gy, gz, bc, 0, 0, hydro_debug_poison(), hydro_debug_drop_group(),
+                           hydro_debug_wait_polls()};
     return hydro_launch<MODE, 1>(level, out, face_flux, dt, dh, status, partials,
                                  int64_t(gx) * gy * gz, p, geo, stream, gz);
 }
@@ -221,7 +227,10 @@ int hydro_advance_level_window(const typename Prec<MODE>::T* window, typename Pr
         }
         if ((zz - zb + gz) % gz >= zn) return GAMER_E_PARAM;
     }
-    const LevelGeom geo = {gx, gy, gz, bc, zb, z0, hydro_debug_poison()};
+    const LevelGeom geo = {gx, gy, gz,
+                           bc, zb, z0,
+                           hydro_debug_poison(), hydro_debug_drop_group(),
+                           hydro_debug_wait_polls()};
     return hydro_launch<MODE, 1>(window, out, face_flux, dt, dh, status, partials,
                                  int64_t(gx) * gy * nz, p, geo, stream, zn);
 }

@@ -391,10 +391,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
         continue;
 
     abort_group:
+        // as hydro_step_kernel: drain the copies in flight, flag this group and
+        // every later one of the CTA, stop
         if (tid == 0) {
             for (int s = 0; s < 2; ++s)
                 if (pending & (1u << s)) mbar_wait(&S.mbar[s], (parity >> s) & 1u);
-            if (status) status[g] = GAMER_ST_INTERNAL_TIMEOUT;
+            mark_abandoned(g, N, status, partials);
         }
         return;
     }

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "abi_common.h"
 #include "gamer_gb300.h"
@@ -117,6 +118,9 @@ struct gamer_pipeline {
     int32_t run_ev_slabs = 0;
     cudaEvent_t run_comp[2] = {nullptr, nullptr};
     cudaEvent_t run_end = nullptr;
+    // a call returned GAMER_E_TIMEOUT with work still queued on the streams:
+    // the next call first waits (bounded) for the streams to drain
+    bool stuck = false;
 };
 
 namespace {
@@ -184,17 +188,48 @@ void release(gamer_pipeline* pl) {
     delete pl;
 }
 
-// Waits for `ev` by polling with a deadline (never blocks indefinitely).
-int wait_event(cudaEvent_t ev, double timeout_s) {
+// Polls `ready` (cudaSuccess / cudaErrorNotReady / error) with a deadline
+// (never blocks indefinitely); after the first polls it sleeps 50 us between
+// them, so a long wait leaves the host core to other work.
+template <class Q>
+int poll_until(Q ready, double timeout_s) {
     const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        const cudaError_t e = cudaEventQuery(ev);
+    for (int n = 0;; ++n) {
+        const cudaError_t e = ready();
         if (e == cudaSuccess) return GAMER_OK;
         if (e != cudaErrorNotReady) return GAMER_E_CUDA;
         const double el =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return GAMER_E_TIMEOUT;
+        if (n >= 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
+}
+
+// Waits for `ev` on pipeline pl; a timeout leaves pl marked stuck.
+int wait_event(gamer_pipeline* pl, cudaEvent_t ev, double timeout_s) {
+    const int rc = poll_until([ev] { return cudaEventQuery(ev); }, timeout_s);
+    if (rc == GAMER_E_TIMEOUT) pl->stuck = true;
+    return rc;
+}
+
+// Start of every call on pl: after a timed-out call, wait (bounded) until
+// the pipeline's three streams are idle, so that no copy of the earlier call
+// is still due to land in host memory; GAMER_E_TIMEOUT (nothing enqueued) if
+// they are not.
+int unstick(gamer_pipeline* pl) {
+    if (!pl->stuck) return GAMER_OK;
+    for (cudaStream_t s : {pl->s_h2d, pl->s_comp, pl->s_d2h}) {
+        const int rc = poll_until([s] { return cudaStreamQuery(s); }, pl->timeout_s);
+        if (rc != GAMER_OK) return rc;
+    }
+    pl->stuck = false;
+    return GAMER_OK;
+}
+
+void CUDART_CB sleep_host(void* seconds) {
+    const double s = *static_cast<double*>(seconds);
+    std::this_thread::sleep_for(std::chrono::duration<double>(s));
+    delete static_cast<double*>(seconds);
 }
 
 }  // namespace
@@ -256,6 +291,7 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
                                            const gh_params* p) {
     using namespace gamer;
     if (!pl) return GAMER_E_NULL;
+    if (const int st = unstick(pl); st != GAMER_OK) return st;
     if (N < 0) return GAMER_E_PARAM;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
@@ -324,7 +360,7 @@ extern "C" int gamer_pipeline_advance_host(gamer_pipeline* pl, const void* in_ho
     }
     // results are in host memory when the last device->host copies are done
     const BufSet& last = pl->set[(nb - 1) % kSets];
-    return wait_event(last.d2h_done, pl->timeout_s);
+    return wait_event(pl, last.d2h_done, pl->timeout_s);
 }
 
 namespace {
@@ -488,7 +524,7 @@ int level_step_resident(gamer_pipeline* pl, const char* hin, char* hout, int32_t
         if (!ok) return GAMER_E_CUDA;
         S.used = true;
     }
-    return wait_event(pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
+    return wait_event(pl, pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
 }
 
 }  // namespace
@@ -505,6 +541,7 @@ extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* le
                                               const gh_params* p, int32_t /*nthreads*/) {
     using namespace gamer;
     if (!pl) return GAMER_E_NULL;
+    if (const int st = unstick(pl); st != GAMER_OK) return st;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
     if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1)) return GAMER_E_PARAM;
@@ -560,7 +597,7 @@ extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* le
             zn = hi - lo + 1;
         }
         // the set's buffers are reused only once its previous results have left
-        if (S.used && (rc = wait_event(S.d2h_done, pl->timeout_s)) != GAMER_OK) return rc;
+        if (S.used && (rc = wait_event(pl, S.d2h_done, pl->timeout_s)) != GAMER_OK) return rc;
         if (!ensure_window(S, size_t(zn_max) * layer_bytes, n_max, e)) {
             cudaGetLastError();
             return GAMER_E_CUDA;
@@ -619,7 +656,7 @@ extern "C" int gamer_pipeline_level_step_host(gamer_pipeline* pl, const void* le
         if (!ok) return GAMER_E_CUDA;
         S.used = true;
     }
-    return wait_event(pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
+    return wait_event(pl, pl->set[(nslab - 1) % kSets].d2h_done, pl->timeout_s);
 }
 
 namespace {
@@ -721,6 +758,7 @@ extern "C" int gamer_pipeline_level_run_host(gamer_pipeline* pl, void* level0, v
                                              double* partials_host, const gh_params* p) {
     using namespace gamer;
     if (!pl) return GAMER_E_NULL;
+    if (const int st = unstick(pl); st != GAMER_OK) return st;
     int rc = check_params(p);
     if (rc != GAMER_OK) return rc;
     if (gx < 0 || gy < 0 || gz < 0 || (bc != 0 && bc != 1) || nsteps < 0) return GAMER_E_PARAM;
@@ -870,13 +908,33 @@ extern "C" int gamer_pipeline_level_run_host(gamer_pipeline* pl, void* level0, v
     if (!ok) return GAMER_E_CUDA;
     pl->d2h_bytes += (dt_host ? 8 * int64_t(nsteps) : 0) + (status_host ? 4 * G : 0) +
                      (partials_host ? 48 * G : 0);
-    return wait_event(pl->run_end, pl->timeout_s * nsteps);
+    return wait_event(pl, pl->run_end, pl->timeout_s * nsteps);
 }
 
 extern "C" int gamer_pipeline_last_bytes(const gamer_pipeline* pl, int64_t* h2d, int64_t* d2h) {
     if (!pl || !h2d || !d2h) return GAMER_E_NULL;
     *h2d = pl->h2d_bytes;
     *d2h = pl->d2h_bytes;
+    return GAMER_OK;
+}
+
+extern "C" int gamer_pipeline_debug_hold(gamer_pipeline* pl, double seconds) {
+    if (!pl) return GAMER_E_NULL;
+    if (!(std::isfinite(seconds) && seconds >= 0.0 && seconds <= 60.0)) return GAMER_E_PARAM;
+    double* arg = new (std::nothrow) double(seconds);
+    if (!arg) return GAMER_E_CUDA;
+    cudaEvent_t ev = pl->set[0].h2d_done;  // reused: no call is in flight here
+    if (cudaLaunchHostFunc(pl->s_h2d, sleep_host, arg) != cudaSuccess) {
+        delete arg;
+        cudaGetLastError();
+        return GAMER_E_CUDA;
+    }
+    if (cudaEventRecord(ev, pl->s_h2d) != cudaSuccess ||
+        cudaStreamWaitEvent(pl->s_comp, ev, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(pl->s_d2h, ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return GAMER_E_CUDA;
+    }
     return GAMER_OK;
 }
 

@@ -40,8 +40,11 @@ __global__ void __launch_bounds__(kRedThreads) dt_pass1(const double* __restrict
         const double m = part[g * 6];
         int l = level ? level[g] : 0;
         l = (l < 0 || l >= L) ? 0 : l;
-        // speeds are >= 0, so the IEEE bit pattern orders like the value
-        if (m > 0.0) atomicMax(&smax[l], static_cast<unsigned long long>(__double_as_longlong(m)));
+        // speeds are >= 0, so the IEEE bit pattern orders like the value; a
+        // NaN (the partials of a group the step abandoned) has a larger bit
+        // pattern than any speed and so wins the maximum
+        if (m > 0.0 || m != m)
+            atomicMax(&smax[l], static_cast<unsigned long long>(__double_as_longlong(m)));
 #pragma unroll
         for (int q = 0; q < 5; ++q) s[q] += part[g * 6 + 1 + q];
     }
@@ -70,8 +73,11 @@ __global__ void __launch_bounds__(kRedThreads) dt_pass2(const double* __restrict
     __shared__ double ssum[kRedThreads / 32][5];
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         double m = 0.0;
-        for (int b = 0; b < B; ++b) m = fmax(m, ws[size_t(b) * (L + 5) + l]);
-        dt_out[l] = (m > 0.0) ? cfl * dh_level[l] / m : 0.0;
+        for (int b = 0; b < B; ++b) {  // a NaN, once met, stays (fmax would drop it)
+            const double x = ws[size_t(b) * (L + 5) + l];
+            m = (x > m || x != x) ? x : m;
+        }
+        dt_out[l] = (m != m) ? m : (m > 0.0) ? cfl * dh_level[l] / m : 0.0;
     }
     double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < B; b += blockDim.x)
@@ -153,14 +159,22 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 __device__ __align__(256) double g_dt_scratch[kNoAllocScratchBytes / sizeof(double)];
 
-// Device address of g_dt_scratch on the current device, looked up once per
-// device (host code only sees a stand-in for the array, never its address).
-double* noalloc_scratch(int dev) {
+// Device address of g_dt_scratch on the current device (host code only sees
+// a stand-in for the array, never its address).  Looked up on every call made
+// outside stream capture, so a module reloaded after cudaDeviceReset is found
+// again; during capture the address of the last lookup on this device is used
+// (the first call on a device must come before any capture).
+double* noalloc_scratch(int dev, cudaStream_t stream) {
     static std::mutex mu;
     static double* addr[64] = {};
     if (dev < 0 || dev >= 64) return nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_dt_scratch) != cudaSuccess) {
             cudaGetLastError();
@@ -184,7 +198,7 @@ extern "C" int gamer_hydro_dt_noalloc(const double* partials, int64_t N, const i
     if (need > kNoAllocScratchBytes) return GAMER_E_WORKSPACE;
     const DeviceInfo d = current_device();
     if (d.status != GAMER_OK) return d.status;
-    double* scratch = noalloc_scratch(d.device);
+    double* scratch = noalloc_scratch(d.device, static_cast<cudaStream_t>(stream));
     if (!scratch) return GAMER_E_CUDA;
     return gamer_hydro_dt(partials, N, level, n_levels, dh_level, cfl, dt_out, totals, dt_group,
                           scratch, kNoAllocScratchBytes, stream);

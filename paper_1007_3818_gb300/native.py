@@ -104,6 +104,8 @@ def lib():
         L.gamer_set_hydro_variant.restype = ctypes.c_int
         L.gamer_set_debug_poison.argtypes = [i32]
         L.gamer_set_debug_poison.restype = ctypes.c_int
+        L.gamer_set_debug_drop_plane.argtypes = [i64, i32]
+        L.gamer_set_debug_drop_plane.restype = ctypes.c_int
         L.gamer_set_hydro_ctas_per_sm.argtypes = [i32, i32]
         L.gamer_set_hydro_ctas_per_sm.restype = ctypes.c_int
         L.gamer_microbench.argtypes = [i32, i64, vp, i64, P(d), vp]
@@ -123,6 +125,8 @@ def lib():
         L.gamer_pipeline_advance_host.restype = ctypes.c_int
         L.gamer_pipeline_set_timeout.argtypes = [vp, d]
         L.gamer_pipeline_set_timeout.restype = ctypes.c_int
+        L.gamer_pipeline_debug_hold.argtypes = [vp, d]
+        L.gamer_pipeline_debug_hold.restype = ctypes.c_int
         L.gamer_pipeline_level_step_host.argtypes = [vp, vp, vp, i32, i32, i32, i32, d, d, vp, vp,
                                                      P(gh_params), i32]
         L.gamer_pipeline_level_step_host.restype = ctypes.c_int
@@ -434,6 +438,14 @@ def gamer_set_debug_poison(on):
     _check(lib().gamer_set_debug_poison(int(on)), "gamer_set_debug_poison")
 
 
+def gamer_set_debug_drop_plane(group, wait_polls=0):
+    """Failure-detection test facility: withhold one input-plane copy of
+    `group` (-1: none) so its bounded on-chip wait runs out after
+    `wait_polls` polls (0: the default bound)."""
+    _check(lib().gamer_set_debug_drop_plane(int(group), int(wait_polls)),
+           "gamer_set_debug_drop_plane")
+
+
 def gamer_set_hydro_variant(variant):
     _check(lib().gamer_set_hydro_variant(int(variant)), "gamer_set_hydro_variant")
 
@@ -495,6 +507,11 @@ class Pipeline:
     def set_timeout(self, seconds):
         _check(lib().gamer_pipeline_set_timeout(self.handle, float(seconds)),
                "gamer_pipeline_set_timeout")
+
+    def debug_hold(self, seconds):
+        """Test facility: hold the pipeline's streams for `seconds` (host sleep)."""
+        _check(lib().gamer_pipeline_debug_hold(self.handle, float(seconds)),
+               "gamer_pipeline_debug_hold")
 
     def advance_host(self, inp, out, face_flux, dt, dh, status, partials, params):
         """Host (CPU, ideally pinned) tensors with the layouts of hydro_advance."""

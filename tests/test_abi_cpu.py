@@ -237,3 +237,14 @@ def test_level_run_binding_checks_tensors_before_the_call(lib):
     with pytest.raises(native.GamerError) as e:
         pl.level_run_host(good, good.clone(), 1, 1, 1, 0, 1, 1e-3, 1.0, 0.5, params)
     assert e.value.code == -1
+
+
+def test_debug_knobs_and_hold_validate_on_the_host(lib):
+    """The failure-detection test facilities check their arguments before any
+    device work: a drop group below -1 or a negative poll limit is
+    GAMER_E_PARAM, a NULL pipeline is GAMER_E_NULL, a hold outside 0..60 s is
+    GAMER_E_PARAM (checked before the pipeline is touched)."""
+    assert lib.gamer_set_debug_drop_plane(-2, 0) == -2
+    assert lib.gamer_set_debug_drop_plane(0, -1) == -2
+    assert lib.gamer_set_debug_drop_plane(-1, 0) == 0          # normal operation
+    assert lib.gamer_pipeline_debug_hold(None, 0.1) == -1

@@ -15,7 +15,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32_1, TOL_F64, rel_l1_fields
+from gpu_util import (TOL_F32_1, TOL_F64, assert_elementwise, elementwise_excess, rel_l1_fields,
+                      rel_l1_per_field)
 from paper_1007_3818_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -77,7 +78,10 @@ def test_uniform_level_full_size_graph_step(fourier_level, mode, tol):
     r_out, r_ff, r_st, r_part = oracle.advance_groups(tiles, dt, dh, gamma=g, nthreads=CORES)
     out, ff, st, part, dt_next, tot, dt_g = _graph_step(lv, mode, g, dt, dh)
     assert rel_l1_fields(out, r_out) <= tol
+    assert max(rel_l1_per_field(out, r_out)) <= tol
     assert rel_l1_fields(ff.reshape(-1, 5, 256), r_ff.reshape(-1, 5, 256)) <= 10 * tol
+    assert_elementwise(out, r_out, mode, "state")
+    assert_elementwise(ff, r_ff, mode, "face flux", state=False)
     assert np.array_equal(st.astype(np.uint32), r_st)
     r_dt, r_tot = oracle.hydro_dt(r_part, [dh], 0.5)
     ptol = 1e-12 if mode == F64 else 10 * tol
@@ -108,10 +112,17 @@ def test_sedov_and_kh_full_size_one_step(problem, mode):
                                               want_flux=False)
     out, _, st, _ = gpu_advance(tiles, dt, dh, g, mode, with_flux=False)
     err = rel_l1_fields(out, r_out)
-    print(f"{problem} mode {mode}: rel-L1 {err:.3e}")
+    per_field = rel_l1_per_field(out, r_out)
+    excess = elementwise_excess(out, r_out, mode)[0]
+    # per field, the KH layer's rho*vz (seeded noise only in vy) is tiny
+    # after one step and carries a large plain relative error of its own; the
+    # magnitude-normalised figure (max over fields) is the one bounded here
+    print(f"{problem} mode {mode}: rel-L1 {err:.3e} (per field "
+          f"{', '.join('%.2e' % x for x in per_field)}), element-wise excess {excess:.3g}")
     if mode == F64:
         assert err <= TOL_F64
         assert np.array_equal(st, r_st)
+        assert excess <= 1.0
     elif problem == "kh":
         assert err <= TOL_F32_1
     else:
@@ -151,7 +162,10 @@ def test_amr_batch_full_size_sampled(mode, tol):
     dts = d_dt.cpu().numpy()[sample]
     r_out, _, r_st, r_part = oracle.advance_groups(host, dts, dh_level[level[sample]], gamma=g,
                                                    nthreads=CORES, want_flux=False)
-    assert rel_l1_fields(out.double().cpu().numpy()[sample], r_out) <= tol
+    got = out.double().cpu().numpy()[sample]
+    assert rel_l1_fields(got, r_out) <= tol
+    assert max(rel_l1_per_field(got, r_out)) <= tol
+    assert_elementwise(got, r_out, mode, "state")
     assert np.array_equal(st.cpu().numpy()[sample].astype(np.uint32), r_st)
     # the per-level dt are CFL-limited by each level's own groups
     assert (dt_level.cpu().numpy() > 0).all()
@@ -228,6 +242,7 @@ def test_streamed_level_full_size_sampled():
                                               nthreads=CORES, want_flux=False)
     got = h_out[torch.from_numpy(sample)].double().numpy()
     assert rel_l1_fields(got, r_out) <= TOL_F32_1
+    assert_elementwise(got, r_out, F32, "state")
     assert np.array_equal(st.numpy()[sample].astype(np.uint32), r_st)
 
 

@@ -567,3 +567,99 @@ def test_counting_scalar_runs_the_same_scheme():
     # 3.19 Riemann solves per updated cell, each a few hundred operations
     assert 500 < per_cell < 5000, counts
     assert counts["sqrt"] / counts["cells"] > 3 * 3.0  # >= 3 sqrt per Roe solve
+
+
+# --------------------------------------------------------------------------
+# Predictor fallback, both options, against a brute-force restatement
+def _np_prim(U, g):
+    rho = U[0]
+    ke = 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho
+    return np.stack([rho, U[1] / rho, U[2] / rho, U[3] / rho, (g - 1.0) * (U[4] - ke)])
+
+
+def _np_cons(W, g):
+    return np.stack([W[0], W[0] * W[1], W[0] * W[2], W[0] * W[3],
+                     W[4] / (g - 1.0) + 0.5 * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3])])
+
+
+def _np_xflux(W, E):
+    m = W[0] * W[1]
+    return np.stack([m, m * W[1] + W[4], m * W[2], m * W[3], (E + W[4]) * W[1]])
+
+
+def _np_admissible(U, g):
+    return (U[0] > 0) & (_np_prim(U, g)[4] > 0)
+
+
+def _brute_force_row(U, lam, g, option, variant="reading"):
+    """One step of a row of cells along x whose state does not vary in y or z
+    (so every transverse slope and flux difference is exactly zero), written
+    out from readings R2-R5: van Leer slopes of the primitives, face values
+    W -/+ s/2, the common half-step increment (lambda/2)(F(W-) - F(W+)), and,
+    where any of the six evolved states is not admissible (R4), option 0: all
+    six become the cell average U; option 1: the un-evolved face states
+    U(W -/+ s/2) (the transverse ones U(W)).  U[5][n+4] with two ghost cells
+    each side; returns (x-face fluxes [17][5], updated row [5][16], cells that
+    fell back).  variant 'evolved' / 'swapped' are plausible mistakes."""
+    W = _np_prim(U, g)
+    n = U.shape[1] - 4
+    a, b = W[:, 1:-1] - W[:, :-2], W[:, 2:] - W[:, 1:-1]       # cells -1 .. n
+    with np.errstate(invalid="ignore", divide="ignore"):
+        s = np.where(a * b > 0, 2.0 * a * b / (a + b), 0.0)
+    Wc = W[:, 1:-1]
+    Wm, Wp = Wc - 0.5 * s, Wc + 0.5 * s
+    Um, Up, Uc = _np_cons(Wm, g), _np_cons(Wp, g), _np_cons(Wc, g)
+    dU = 0.5 * lam * (_np_xflux(Wm, Um[4]) - _np_xflux(Wp, Up[4]))
+    xm, xp, yz = Um + dU, Up + dU, Uc + dU
+    bad = ~(_np_admissible(xm, g) & _np_admissible(xp, g) & _np_admissible(yz, g))
+    if option == 0:
+        keep_m = keep_p = U[:, 1:-1]
+    elif variant == "evolved":
+        keep_m, keep_p = xm, xp
+    elif variant == "swapped":
+        keep_m, keep_p = Up, Um
+    else:
+        keep_m, keep_p = Um, Up
+    xm = np.where(bad, keep_m, xm)
+    xp = np.where(bad, keep_p, xp)
+    F = np.array([oracle.roe_flux(0, xp[:, f], xm[:, f + 1], g)[0] for f in range(n + 1)])
+    out = U[:, 2:-2] - lam * (F[1:] - F[:-1]).T
+    return F, out, np.nonzero(bad)[0] - 1
+
+
+@pytest.mark.parametrize("option", [0, 1])
+def test_predictor_fallback_matches_brute_force(option):
+    """A near-vacuum cell between diverging flows: its half-step states are
+    inadmissible, so the predictor fallback fires there.  The oracle's face
+    fluxes (nine-plane layout: x faces 0, 8, 16; face 8 lies beside the
+    fallback cell) and its updated row equal the brute-force restatement of
+    the readings, for both options; the plausible mistakes of option 1 --
+    keeping the evolved states, or each cell's face values swapped -- give
+    results far from the oracle's."""
+    g, dh, dt = 1.4, 1 / 16, 0.02
+    n = 20
+    rho, u, p = np.ones(n), np.zeros(n), np.full(n, 0.1)
+    rho[10], p[10] = 1e-3, 1e-4          # cell 8 of the row
+    u[:10], u[11:] = -2.0, 2.0
+    row = wl.to_conserved(rho, u, 0 * rho, 0 * rho, p, g)              # [5][20]
+    box = np.broadcast_to(row[:, None, None, :], (5, 6, 6, n)).copy()  # 16 x 2 x 2 cells
+    out, faces, st, _ = oracle.advance_box(box, dt, dh, gamma=g, predictor_fallback=option,
+                                           flux_layout=1)
+    F, bf_out, fell = _brute_force_row(row, dt / dh, g, option)
+    assert 8 in fell and st & oracle.ST_PREDICTOR_FALLBACK
+    # each face against its own magnitude (face 8, beside the near vacuum,
+    # carries fluxes ~1e-3 next to ~4 on the outer faces)
+    for k, f in enumerate((0, 8, 16)):
+        sc = np.abs(F[f]).max()
+        assert np.abs(faces[k] - F[f][:, None, None]).max() <= 1e-12 * sc, (f, faces[k], F[f])
+    assert np.abs(out - bf_out[:, None, None, :]).max() <= 1e-12 * np.abs(bf_out).max()
+    sc8 = np.abs(F[8]).max()
+    if option == 1:
+        for wrong in ("evolved", "swapped"):
+            Fw, ow, _ = _brute_force_row(row, dt / dh, g, 1, variant=wrong)
+            assert np.abs(Fw[8] - F[8]).max() > 1e-2 * sc8, wrong
+            assert (np.abs(ow - bf_out) / np.abs(bf_out).clip(1e-300)).max() > 1e-2, wrong
+    else:
+        F1, o1, _ = _brute_force_row(row, dt / dh, g, 1)
+        assert np.abs(F1[8] - F[8]).max() > 1e-2 * sc8
+        assert (np.abs(o1 - bf_out) / np.abs(bf_out).clip(1e-300)).max() > 1e-2

@@ -69,12 +69,21 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls(native):
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(native):
     import torch
-    part = torch.zeros((4, 6), device="cuda", dtype=torch.float64)
+    N = 200000
+    # buffers sized for the call, so that even a regressed size check could
+    # not read or write out of bounds
+    part = torch.zeros((N, 6), device="cuda", dtype=torch.float64)
+    level = torch.zeros(N, device="cuda", dtype=torch.int32)
     dh = torch.ones(64, device="cuda", dtype=torch.float64)
     out = torch.zeros(64, device="cuda", dtype=torch.float64)
+    dt_group = torch.zeros(N, device="cuda", dtype=torch.float64)
     # 64 levels and 200,000 groups need more than the 64 KiB scratch; the call
     # is rejected on the host before anything is launched
-    rc = native.lib().gamer_hydro_dt_noalloc(ctypes.c_void_p(part.data_ptr()), 200000, None, 64,
+    rc = native.lib().gamer_hydro_dt_noalloc(ctypes.c_void_p(part.data_ptr()), N,
+                                             ctypes.c_void_p(level.data_ptr()), 64,
                                              ctypes.c_void_p(dh.data_ptr()), 0.5,
-                                             ctypes.c_void_p(out.data_ptr()), None, None, None)
+                                             ctypes.c_void_p(out.data_ptr()), None,
+                                             ctypes.c_void_p(dt_group.data_ptr()), None)
     assert rc == -7  # GAMER_E_WORKSPACE
+    torch.cuda.synchronize()
+    assert not out.any() and not dt_group.any()
