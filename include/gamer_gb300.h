@@ -60,7 +60,8 @@ extern "C" {
 
 /* ---- precision modes ---- */
 #define GAMER_MODE_F32 0   /* FP32 storage and arithmetic                                     */
-#define GAMER_MODE_MIXED 1 /* FP32 storage/arithmetic, pressure E - |m|^2/(2 rho) in FP64     */
+#define GAMER_MODE_MIXED 1 /* FP32 storage/arithmetic; pressure E - |m|^2/(2 rho) in FP64 where
+                              the kinetic energy is more than half of E (high Mach)       */
 #define GAMER_MODE_F64 2   /* FP64 storage and arithmetic                                     */
 #define GAMER_MODE_FF 3    /* FP32 storage/arithmetic, pressure recovery in float-float        */
 
@@ -119,8 +120,14 @@ typedef struct gh_params {
  *   p         scheme parameters (host pointer).
  *   stream    cudaStream_t.
  * _f32, _mixed and _ff take float arrays, _f64 double arrays.  In _mixed mode
- * every recovery of the pressure from the conserved state (where E - rho v^2/2
- * cancels in high-Mach cells) is done in FP64; everything else in FP32.  _ff
+ * FP64 is used only where stability needs it: a recovery of the pressure from
+ * the conserved state is done in FP64 where |m|^2/(2 rho) > E/2 (high-Mach
+ * cells, where E - rho v^2/2 cancels) and in FP32 elsewhere, with gamma - 1
+ * held as a float pair so that it brings no rounding bias (there the result
+ * is within a few ulps of the FP64 recovery); a test rho E - |m|^2/2 > 0 is
+ * decided in FP32 when the FP32 difference is larger than 2^-20 (|rho E| +
+ * |m|^2/2), so certainly of the right sign, and in FP64 otherwise; everything
+ * else is FP32 (the group reductions are FP64 in every mode).  _ff
  * does the same recoveries (and the rho E - |m|^2/2 > 0 tests) in float-float
  * FP32 arithmetic: |m|^2 exact by FMA products and TwoSum, 1/rho refined to
  * about 2^-46, E - |m|^2/(2 rho) by TwoSum -- as accurate as the FP64 recovery
@@ -301,6 +308,34 @@ int gamer_level_graph_launch(gamer_level_graph* g, void* stream);
 int gamer_level_graph_destroy(gamer_level_graph* g);
 
 /*
+ * gamer_batch_graph_create: one step of a batch of N patch groups from uneven
+ * AMR levels (each group with its own dt and dh; paper Sec. 2: patches of all
+ * levels are batched to the GPU solver) as one CUDA graph: the time step of
+ * every level from the partials of the previous step (gamer_hydro_dt with the
+ * level map; dt_group[g] = dt_level[level[g]]), then one persistent launch of
+ * gamer_hydro_advance_<mode> over all N groups, whose partials feed the next
+ * replay.  Launched with gamer_level_graph_launch, destroyed with
+ * gamer_level_graph_destroy.  A replay equals the two calls made directly, bit
+ * for bit.
+ *   in [N][5][20]^3 ghost-padded tiles, out [N][5][16]^3, face_flux as
+ *   gamer_hydro_advance_* or NULL, dt_group [N] (written by the reduction),
+ *   dh_group [N], level [N] int32 in [0, n_levels) or NULL, status [N] or NULL,
+ *   partials [N][6] (must hold the partials of the state the first replay
+ *   starts from, e.g. from a zero-dt step), dh_level and dt_level [n_levels],
+ *   totals [5] or NULL, workspace of gamer_hydro_dt_workspace_bytes(N,
+ *   n_levels) bytes.  All device memory, outliving the graph; mode
+ *   GAMER_MODE_*; p->cfl is the Courant number.  Returns GAMER_E_PARAM for N <
+ *   1, n_levels outside 1..64 or a bad mode / parameter, GAMER_E_WORKSPACE for
+ *   a short workspace, and the errors of the captured calls.
+ */
+int gamer_batch_graph_create(int32_t mode, const void* in, void* out, void* face_flux,
+                             double* dt_group, const double* dh_group, const int32_t* level,
+                             int32_t n_levels, uint32_t* status, double* partials, int64_t N,
+                             const gh_params* p, const double* dh_level, double* dt_level,
+                             double* totals, void* workspace, size_t workspace_bytes,
+                             gamer_level_graph** out_graph);
+
+/*
  * Streamed host pipeline (the paper overlaps CPU, GPU and disk work, Sec. 2
  * and Sec. 3; here host->device copies, hydro steps and device->host copies
  * of successive batches overlap on three streams).
@@ -418,6 +453,22 @@ int gamer_fill_ghosts_uniform_host_f32(const float* level, float* in, int32_t gx
 int gamer_fill_ghosts_uniform_host_f64(const double* level, double* in, int32_t gx, int32_t gy,
                                        int32_t gz, int32_t bc, int32_t nthreads);
 int gamer_pipeline_destroy(gamer_pipeline* pl);
+
+/*
+ * Host memory for the host-resident levels of gamer_pipeline_* (paper Sec. 3
+ * keeps out-of-core data in host memory): gamer_host_alloc maps `bytes`
+ * (rounded up to the transparent-huge-page size), asks for huge-page backing,
+ * faults every page in with nthreads host threads (<= 0: all; the memory is
+ * zero-filled) and page-locks it for CUDA (cudaHostRegister), so that device
+ * copies from and to it run asynchronously at full link speed.  Huge pages
+ * keep the translations that the copies walk few whatever the state of the
+ * host's free memory.  Synchronous; returns GAMER_E_PARAM for 0 or more than
+ * 2^46 bytes, GAMER_E_CUDA when the mapping or the registration fails.
+ * gamer_host_free releases a pointer gamer_host_alloc returned (GAMER_E_PARAM
+ * for any other); no device work may still use it.
+ */
+int gamer_host_alloc(size_t bytes, int32_t nthreads, void** out);
+int gamer_host_free(void* ptr);
 
 /* Message for a GAMER_E* return code (static string). */
 const char* gamer_strerror(int code);

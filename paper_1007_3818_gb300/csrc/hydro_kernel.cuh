@@ -112,17 +112,44 @@ __device__ __forceinline__ int flux_plane(int dir, int b, int flux9) {
 constexpr int kFluxPlane = 5 * 256;  // one plane: [5][16][16]
 
 // ---------------------------------------------------------------------------
-// Pressure from a conserved state, given 1/rho in T.  MIXED recovers it in
-// FP64: 1/rho from the FP32 seed plus one Newton step, then E - |m|^2/(2 rho).
+// Selective FP64 in the mixed mode.  The pressure p = (gamma - 1)(E - ke),
+// ke = |m|^2 / (2 rho), is recovered in FP32 with gamma - 1 held as a
+// (hi, lo) float pair, so no systematic bias from rounding gamma - 1 enters;
+// its relative error is then at most about (2 + 6 r / (1 - r)) u, r = ke / E,
+// u = 2^-24 (ke carries ~6 roundings, rcp.approx included, and the
+// subtraction magnifies them by ke / (E - ke)).  Where the kinetic energy is
+// more than half the total (r > 1/2: the flow is supersonic to within a
+// factor of order one) that bound passes 8 u and grows without limit as
+// E - ke cancels, so there p is recovered in FP64 instead: 1/rho from the
+// FP32 seed plus one Newton step, E - ke in FP64, one rounding.  Below the
+// threshold the FP32 result is within a few ulps of the FP64 one.
+constexpr float kMixedKeFraction = 0.5f;
+
+static __device__ __noinline__ float pressure_fp64(float r, float m1, float m2, float m3, float E,
+                                            float ir, double gm1p) {
+    const double rd = r;
+    double ird = ir;
+    ird = fma(ird, fma(-rd, ird, 1.0), ird);
+    const double a = m1, b = m2, c = m3;
+    const double ke = 0.5 * (a * a + b * b + c * c) * ird;
+    return static_cast<float>(gm1p * (static_cast<double>(E) - ke));
+}
+
+// rho E - |m|^2 / 2 > 0 in FP64 (the undecided cases of admissible<MIXED>)
+static __device__ __noinline__ bool positive_fp64(float r, float m1, float m2, float m3, float E) {
+    const double a = m1, b = m2, c = m3;
+    return (double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0;
+}
+
+// Pressure from a conserved state, given 1/rho in T.  MIXED: the selective
+// recovery above.
 template <int MODE, class T, class P>
 __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KConst<T, P>& kc) {
     if constexpr (MODE == GAMER_MODE_MIXED) {
-        const double rd = r;
-        double ird = ir;
-        ird = fma(ird, fma(-rd, ird, 1.0), ird);
-        const double a = m1, b = m2, c = m3;
-        const double ke = 0.5 * (a * a + b * b + c * c) * ird;
-        return static_cast<T>(kc.gm1p * (static_cast<double>(E) - ke));
+        const float ke = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3) * ir;
+        if (ke > kMixedKeFraction * E) return pressure_fp64(r, m1, m2, m3, E, ir, kc.gm1p);
+        const float d = E - ke;
+        return fmaf(kc.gm1, d, kc.gm1_lo * d);
     } else if constexpr (MODE == GAMER_MODE_FF) {
         // the same recovery in float-float: 1/rho = ir (1 + d), d = 1 - rho ir
         // from one FMA; |m|^2 ir exactly as p + pe; E - ke by TwoSum
@@ -179,13 +206,19 @@ __device__ __forceinline__ void apply_floors(T o[5], T& ir, T& p, const KConst<T
     }
 }
 
-// rho > 0 and p > 0, tested as rho > 0 and rho E - |m|^2 / 2 > 0 (no division);
-// MIXED evaluates the difference in FP64.
+// rho > 0 and p > 0, tested as rho > 0 and rho E - |m|^2 / 2 > 0 (no division).
+// MIXED takes the decision of the FP64 difference: the FP32 difference d
+// carries an error below 4 u (|rho E| + |m|^2 / 2), so where |d| exceeds
+// 2^-20 (|rho E| + |m|^2 / 2) its sign is the FP64 sign; only the cases
+// closer to zero are decided in FP64.
 template <int MODE, class T>
 __device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
     if constexpr (MODE == GAMER_MODE_MIXED) {
-        const double a = m1, b = m2, c = m3;
-        return (r > T(0)) & ((double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0);
+        const float h = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3);
+        const float re = r * E;
+        const float d = re - h;
+        if (fabsf(d) > 0x1p-20f * (fabsf(re) + h)) return (r > 0.0f) & (d > 0.0f);
+        return (r > 0.0f) & positive_fp64(r, m1, m2, m3, E);
     } else if constexpr (MODE == GAMER_MODE_FF) {
         float se, ee, t;
         const float s = sq3_ff(m1, m2, m3, se);

@@ -130,6 +130,98 @@ extern "C" int gamer_level_graph_create(int32_t mode, void* level_a, void* level
     return GAMER_OK;
 }
 
+namespace {
+
+// One step of an uneven AMR batch: dt per level from the partials of the
+// previous step, scattered to the groups, then the persistent step of all N
+// groups (whose partials feed the next step).
+int enqueue_batch_step(int mode, const void* in, void* out, void* ff, double* dt_group,
+                       const double* dh_group, const int32_t* level, int32_t n_levels,
+                       uint32_t* status, double* partials, int64_t N, const gh_params* p,
+                       const double* dh_level, double* dt_level, double* totals, void* ws,
+                       size_t ws_bytes, cudaStream_t s) {
+    int rc = gamer_hydro_dt(partials, N, level, n_levels, dh_level, p->cfl, dt_level, totals,
+                            dt_group, ws, ws_bytes, s);
+    if (rc != GAMER_OK) return rc;
+    if (mode == GAMER_MODE_F32)
+        return gamer_hydro_advance_f32((const float*)in, (float*)out, (float*)ff, dt_group,
+                                       dh_group, status, partials, N, p, s);
+    if (mode == GAMER_MODE_MIXED)
+        return gamer_hydro_advance_mixed((const float*)in, (float*)out, (float*)ff, dt_group,
+                                         dh_group, status, partials, N, p, s);
+    if (mode == GAMER_MODE_FF)
+        return gamer_hydro_advance_ff((const float*)in, (float*)out, (float*)ff, dt_group,
+                                      dh_group, status, partials, N, p, s);
+    return gamer_hydro_advance_f64((const double*)in, (double*)out, (double*)ff, dt_group,
+                                   dh_group, status, partials, N, p, s);
+}
+
+// Captures `enqueue` (a callable taking the capture stream) into a new graph
+// handle.
+template <class F>
+int capture(F enqueue, gamer_level_graph** out) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GAMER_E_CUDA;
+    gamer_level_graph* h = new (std::nothrow) gamer_level_graph();
+    if (!h) {
+        cudaStreamDestroy(s);
+        return GAMER_E_CUDA;
+    }
+    int rc = GAMER_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = GAMER_E_CUDA;
+    } else {
+        rc = enqueue(s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (rc == GAMER_OK && e != cudaSuccess) rc = GAMER_E_CUDA;
+        h->graph = g;
+        if (rc == GAMER_OK && cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess)
+            rc = GAMER_E_CUDA;
+    }
+    cudaStreamDestroy(s);
+    if (rc != GAMER_OK) {
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        delete h;
+        cudaGetLastError();
+        return rc;
+    }
+    *out = h;
+    return GAMER_OK;
+}
+
+}  // namespace
+
+extern "C" int gamer_batch_graph_create(int32_t mode, const void* in, void* out, void* face_flux,
+                                        double* dt_group, const double* dh_group,
+                                        const int32_t* level, int32_t n_levels, uint32_t* status,
+                                        double* partials, int64_t N, const gh_params* p,
+                                        const double* dh_level, double* dt_level, double* totals,
+                                        void* workspace, size_t workspace_bytes,
+                                        gamer_level_graph** out_graph) {
+    using namespace gamer;
+    if (!out_graph) return GAMER_E_NULL;
+    *out_graph = nullptr;
+    if (mode < 0 || mode > 3 || N < 1 || n_levels < 1 || n_levels > 64) return GAMER_E_PARAM;
+    int rc = check_params(p);
+    if (rc != GAMER_OK) return rc;
+    if (!(std::isfinite(p->cfl) && p->cfl > 0.0)) return GAMER_E_PARAM;
+    if (!in || !out || !dt_group || !dh_group || !partials || !dh_level || !dt_level)
+        return GAMER_E_NULL;
+    if (workspace_bytes < gamer_hydro_dt_workspace_bytes(N, n_levels) || !workspace)
+        return GAMER_E_WORKSPACE;
+    const DeviceInfo d = current_device();
+    if (d.status != GAMER_OK) return d.status;
+    return capture(
+        [&](cudaStream_t s) {
+            return enqueue_batch_step(mode, in, out, face_flux, dt_group, dh_group, level,
+                                      n_levels, status, partials, N, p, dh_level, dt_level,
+                                      totals, workspace, workspace_bytes, s);
+        },
+        out_graph);
+}
+
 extern "C" int gamer_level_graph_launch(gamer_level_graph* h, void* stream) {
     if (!h || !h->exec) return GAMER_E_NULL;
     return cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess

@@ -114,6 +114,10 @@ def lib():
                                                i32, P(gh_params), vp, vp, vp, vp,
                                                ctypes.c_size_t, P(vp)]
         L.gamer_level_graph_create.restype = ctypes.c_int
+        L.gamer_batch_graph_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, i32, vp, vp, i64,
+                                               P(gh_params), vp, vp, vp, vp, ctypes.c_size_t,
+                                               P(vp)]
+        L.gamer_batch_graph_create.restype = ctypes.c_int
         L.gamer_level_graph_launch.argtypes = [vp, vp]
         L.gamer_level_graph_launch.restype = ctypes.c_int
         L.gamer_level_graph_destroy.argtypes = [vp]
@@ -141,6 +145,10 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [vp, vp, i32, i32, i32, i32, i32]
             f.restype = ctypes.c_int
+        L.gamer_host_alloc.argtypes = [ctypes.c_size_t, i32, P(vp)]
+        L.gamer_host_alloc.restype = ctypes.c_int
+        L.gamer_host_free.argtypes = [vp]
+        L.gamer_host_free.restype = ctypes.c_int
         L.gamer_pipeline_destroy.argtypes = [vp]
         L.gamer_pipeline_destroy.restype = ctypes.c_int
         _lib = L
@@ -494,6 +502,39 @@ class LevelGraph:
             pass
 
 
+class BatchGraph(LevelGraph):
+    """gamer_batch_graph_create: one step of an uneven AMR batch (dt per level
+    from the previous partials, then the persistent step of all groups) per
+    launch.  Keeps references to the tensors it was captured with."""
+
+    def __init__(self, mode, inp, out, face_flux, dt_group, dh_group, level, n_levels, status,
+                 partials, params, dh_level, dt_level, totals, workspace):
+        import torch
+        T = torch.float64 if mode == GAMER_MODE_F64 else torch.float32
+        N = int(inp.shape[0])
+        args = [_ptr(inp, T, (5, 20, 20, 20), "in"), _ptr(out, T, (5, 16, 16, 16), "out"),
+                _ptr(face_flux, T, (FLUX_PLANES[params.flux_layout], 5, 16, 16), "face_flux"),
+                _ptr(dt_group, torch.float64, (), "dt_group"),
+                _ptr(dh_group, torch.float64, (), "dh_group"),
+                _ptr(level, torch.int32, (), "level")]
+        for t, nm in ((out, "out"), (dt_group, "dt_group"), (dh_group, "dh_group"),
+                      (level, "level"), (status, "status"), (partials, "partials")):
+            if t is not None and int(t.shape[0]) != N:
+                raise GamerError(-2, f"{nm} has {int(t.shape[0])} groups, in has {N}")
+        self._keep = (inp, out, face_flux, dt_group, dh_group, level, status, partials, dh_level,
+                      dt_level, totals, workspace, params)
+        h = ctypes.c_void_p()
+        ws_bytes = workspace.numel() * workspace.element_size()
+        rc = lib().gamer_batch_graph_create(
+            int(mode), *args, int(n_levels), _ptr(status, torch.int32, (), "status"),
+            _ptr(partials, torch.float64, (6,), "partials"), N, ctypes.byref(params),
+            _ptr(dh_level, torch.float64, (), "dh_level"),
+            _ptr(dt_level, torch.float64, (), "dt_level"), _ptr(totals, torch.float64),
+            _ptr(workspace), ws_bytes, ctypes.byref(h))
+        _check(rc, "gamer_batch_graph_create")
+        self.handle = h
+
+
 class Pipeline:
     """gamer_pipeline_*: host-resident batches streamed through the GPU."""
 
@@ -602,3 +643,33 @@ def gamer_fill_ghosts_uniform_host(level, inp, gx, gy, gz, bc, nthreads=0):
     rc = getattr(lib(), name)(ctypes.c_void_p(lv.ctypes.data), ctypes.c_void_p(out.ctypes.data),
                               gx, gy, gz, bc, int(nthreads))
     _check(rc, name)
+
+
+class HostBuffer:
+    """gamer_host_alloc: page-locked, huge-page-backed host memory for levels
+    streamed through the device.  ``.tensor`` views it with the given shape and
+    dtype (a CPU tensor); call close() (or drop the object) once no device work
+    uses it any more."""
+
+    def __init__(self, shape, dtype, nthreads=0):
+        import math
+        import torch
+        self.nbytes = int(math.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+        p = ctypes.c_void_p()
+        _check(lib().gamer_host_alloc(self.nbytes, int(nthreads), ctypes.byref(p)),
+               "gamer_host_alloc")
+        self.ptr = p
+        arr = (ctypes.c_uint8 * self.nbytes).from_address(p.value)
+        self.tensor = torch.frombuffer(arr, dtype=dtype).view(*shape)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self.tensor = None
+            lib().gamer_host_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -248,3 +248,15 @@ def test_debug_knobs_and_hold_validate_on_the_host(lib):
     assert lib.gamer_set_debug_drop_plane(0, -1) == -2
     assert lib.gamer_set_debug_drop_plane(-1, 0) == 0          # normal operation
     assert lib.gamer_pipeline_debug_hold(None, 0.1) == -1
+
+
+def test_host_alloc_validates_on_the_host(lib):
+    """gamer_host_alloc / gamer_host_free reject bad arguments before mapping
+    anything; a pointer the allocator did not return is refused."""
+    p = ctypes.c_void_p()
+    assert lib.gamer_host_alloc(0, 1, ctypes.byref(p)) == -2
+    assert lib.gamer_host_alloc(1 << 47, 1, ctypes.byref(p)) == -2
+    assert lib.gamer_host_alloc(4096, 1, None) == -1
+    assert lib.gamer_host_free(None) == -1
+    buf = ctypes.create_string_buffer(64)
+    assert lib.gamer_host_free(ctypes.cast(buf, ctypes.c_void_p)) == -2

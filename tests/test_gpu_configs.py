@@ -332,3 +332,79 @@ def test_pipeline_level_run_edge_cases(mode):
     ref.close()
     assert torch.equal(l1, out) and torch.equal(r_part, part) and torch.equal(r_st, st)
     assert float(r_dt[0]) == dt
+
+
+@pytest.mark.parametrize("mode", [F32, F64], ids=["f32", "f64"])
+def test_amr_batch_graph_replays_equal_direct_calls(mode):
+    """Config 4 (54,000 tiles on three levels, shuffled): three replays of the
+    captured batch step (dt per level from the previous partials, scatter,
+    persistent step of all groups) equal three rounds of the same calls made
+    directly, bit for bit -- states, face fluxes, status, partials, dt per
+    level and per group."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    base, origins, level, dh_level = wl.amr_batch_parts()
+    N = len(level)
+    T = torch.float64 if mode == F64 else torch.float32
+    tiles = wl.window_tiles_torch(base, origins, "cuda").to(T)
+    d_level = torch.as_tensor(level, device="cuda")
+    d_dhl = torch.as_tensor(dh_level, device="cuda")
+    d_dh = d_dhl[d_level.long()].contiguous()
+    params = native.make_params(g, cfl=0.5)
+    ws = torch.empty(native.gamer_hydro_dt_workspace_bytes(N, 3), device="cuda", dtype=torch.uint8)
+
+    def fresh():
+        bufs = {"out": torch.empty((N, 5, 16, 16, 16), device="cuda", dtype=T),
+                "ff": torch.empty((N, 6, 5, 16, 16), device="cuda", dtype=T),
+                "dt": torch.zeros(N, device="cuda", dtype=torch.float64),
+                "st": torch.zeros(N, device="cuda", dtype=torch.int32),
+                "part": torch.empty((N, 6), device="cuda", dtype=torch.float64),
+                "dtl": torch.zeros(3, device="cuda", dtype=torch.float64),
+                "tot": torch.zeros(5, device="cuda", dtype=torch.float64)}
+        # partials of the initial state (a zero-dt step)
+        native.hydro_advance(mode, tiles, bufs["out"], None, bufs["dt"], d_dh, None, bufs["part"],
+                             params)
+        return bufs
+
+    a, b = fresh(), fresh()
+    graph = native.BatchGraph(mode, tiles, a["out"], a["ff"], a["dt"], d_dh, d_level, 3, a["st"],
+                              a["part"], params, d_dhl, a["dtl"], a["tot"], ws)
+    ws_b = torch.empty_like(ws)
+    snaps = []
+    for _ in range(3):
+        graph.launch()
+        native.gamer_hydro_dt(b["part"], d_level, d_dhl, 0.5, b["dtl"], b["tot"], b["dt"], ws_b)
+        native.hydro_advance(mode, tiles, b["out"], b["ff"], b["dt"], d_dh, b["st"], b["part"],
+                             params)
+        torch.cuda.synchronize()
+        snaps.append(float(a["dtl"][0]))
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
+    graph.close()
+    assert (a["dtl"] > 0).all() and snaps[0] > 0
+
+
+def test_host_alloc_levels_stream_like_pinned_ones():
+    """Levels in gamer_host_alloc memory (huge-page backed, page-locked) go
+    through the multi-step pipeline exactly as torch-pinned levels do."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g, dh, cfl = 5 / 3, 1 / 64, 0.5
+    lv = wl.level_to_groups(wl.fourier_level(n=64, seed=12, gamma=g)).astype(np.float32)
+    shape = lv.shape
+    bufs = [native.HostBuffer(shape, torch.float32) for _ in range(2)]
+    assert not bufs[0].tensor.any()                # zero-filled
+    bufs[0].tensor.copy_(torch.from_numpy(lv))
+    pinned = [torch.from_numpy(lv).pin_memory(), torch.empty(shape).pin_memory()]
+    res = []
+    for pair in ([b.tensor for b in bufs], pinned):
+        pl = native.Pipeline(F32, 32, with_flux=False)
+        part = torch.zeros((64, 6), dtype=torch.float64)
+        pl.level_run_host(pair[0], pair[1], 4, 4, 4, 0, 3, 1e-3, dh, cfl, native.make_params(g),
+                          None, None, part)
+        pl.close()
+        res.append((pair[1].clone(), part))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    for b in bufs:
+        b.close()

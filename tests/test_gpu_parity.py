@@ -658,3 +658,38 @@ def test_fused_level_rejects_in_place_update():
     with pytest.raises(native.GamerError):
         native.hydro_advance_level(F32, lv, lv, None, 2, 2, 2, 0, d, d, None, None,
                                    native.make_params(1.4))
+
+
+# --------------------------------------------------------------------------
+# Selective FP64 in the mixed mode: FP64 pressure recovery only where the
+# kinetic energy is more than half of E
+def test_selective_fp64_recovery_takes_both_branches_in_one_tile():
+    """One group whose flow is Mach ~3 along x in one half (|m|^2/(2 rho) > E/2:
+    the FP64 branch) and Mach ~0.3 in the other (the FP32 branch), joined
+    smoothly, with a density and pressure wave.  The mixed mode meets the
+    parity bars against the oracle (rel-L1 and element-wise), and agrees
+    value by value with the float-float mode, which recovers every pressure
+    to FP64 accuracy, to within a few ulps of each field's scale."""
+    g = 5 / 3
+    x = (np.arange(20) - 2 + 0.5) / 16
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")                  # [k][j][i]
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Z)
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * Y)
+    c = np.sqrt(g * p / rho)
+    mach = 0.3 + 2.7 * 0.5 * (1 + np.tanh((0.5 - Y) / 0.08))
+    U = wl.to_conserved(rho, mach * c, 0.1 * c, -0.05 * c, p, g)[None]
+    host = U.astype(np.float32).astype(np.float64)
+    ke = 0.5 * (host[0, 1] ** 2 + host[0, 2] ** 2 + host[0, 3] ** 2) / host[0, 0]
+    high = ke > 0.5 * host[0, 4]
+    interior = high[2:18, 2:18, 2:18]
+    assert 0.3 < interior.mean() < 0.7                # both branches, in one tile
+    dt = 0.2 / (16 * 4.0)                              # CFL ~0.2 at the fast side
+    compare_step(host, dt, 1 / 16, g, MIXED, TOL_F32_1)
+    mx, fx, sx, _ = gpu_advance(host, dt, 1 / 16, g, MIXED)
+    mf, ff_, sf, _ = gpu_advance(host, dt, 1 / 16, g, FF)
+    assert np.array_equal(sx, sf)
+    from gpu_util import elementwise_excess
+    ex_state = elementwise_excess(mx, mf, FF)[0] * 256 / 16      # in units of 16 eps
+    ex_flux = elementwise_excess(fx, ff_, FF, state=False)[0] * 256 / 16
+    print(f"mixed vs float-float: {ex_state:.3g} / {ex_flux:.3g} x (16 eps (|b| + S))")
+    assert ex_state <= 1.0 and ex_flux <= 1.0
