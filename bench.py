@@ -220,6 +220,23 @@ def tiled_sources(gx, gb):
     return ((bz % gb) * gb + (by % gb)) * gb + (bx % gb)
 
 
+def periodic_tiles(groups, gx, out=None):
+    """The 20^3 ghost-padded input of every group of a periodic gx^3-group
+    level (the level's own cells, wrapped), sliced group by group out of the
+    padded level -- plain indexing, independent of the CUDA path.  `out`
+    (reused between steps) avoids faulting in a new array every time."""
+    import numpy as np
+    from paper_1007_3818_gb300 import workloads as wl
+    box = wl.groups_to_level(groups, gx, gx, gx)                        # [5][n][n][n]
+    pad = np.pad(box, ((0, 0), (2, 2), (2, 2), (2, 2)), mode="wrap")
+    if out is None:
+        out = np.empty((gx ** 3, 5, 20, 20, 20), dtype=groups.dtype)
+    for g in range(gx ** 3):
+        bz, by, bx = g // (gx * gx), (g // gx) % gx, g % gx
+        out[g] = pad[:, 16 * bz:16 * bz + 20, 16 * by:16 * by + 20, 16 * bx:16 * bx + 20]
+    return out
+
+
 def uniform256_level():
     from paper_1007_3818_gb300 import workloads as wl
     return wl.level_to_groups(wl.fourier_level(n=256, seed=SEED, gamma=GAMMA))
@@ -268,14 +285,14 @@ def oracle_precision_reference(problem, n, steps, cfl):
     G0 = wl.level_to_groups(U).astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     ref, dts = G0, []
-    tiles = oracle.fill_ghosts_uniform(ref, gx, gx, gx, 0)
+    tiles = periodic_tiles(ref, gx)
     _, _, _, part = oracle.advance_groups(tiles, 0.0, dh, gamma=GAMMA, nthreads=cores,
                                           want_flux=False)
     for _ in range(steps):
         dt = oracle.hydro_dt(part, [dh], cfl)[0][0]
         ref, _, _, part = oracle.advance_groups(tiles, dt, dh, gamma=GAMMA, nthreads=cores,
                                                 want_flux=False)
-        tiles = oracle.fill_ghosts_uniform(ref, gx, gx, gx, 0)
+        tiles = periodic_tiles(ref, gx, out=tiles)
         dts.append(dt)
     return G0, dts, ref, time.perf_counter() - t0
 
@@ -417,6 +434,12 @@ class LevelRun:
         return [float(abs(a - b) / max(abs(b), 1e-300)) for a, b in zip(tot, self.tot0)]
 
 
+def tuned_record(t):
+    return {"ctas_per_sm": t["ctas_per_sm"], "variant": t["variant"],
+            "threads_per_group": t["threads_per_group"],
+            "candidates_ms (ctas x variant)": t["all"]}
+
+
 def tune_level(native, run):
     from paper_1007_3818_gb300 import tune
     return tune.tune_hydro_level(run.mode, run.cur[0], run.cur[1], run.ff, run.gx, run.gx,
@@ -478,7 +501,7 @@ def headline(args, native, dist, dev, world, rank):
     cells = run.G * GROUP_CELLS
     rec = {"value": world * cells * args.steps / el, "ms_per_step": el / args.steps * 1e3,
            "kernel_ms": kms, "clocks": clk, "groups": run.G, "cells_per_step": cells,
-           "tuned": {"ctas_per_sm": tuned["ctas_per_sm"], "candidates_ms": tuned["all"]},
+           "tuned": tuned_record(tuned),
            "status_or": int(np.bitwise_or.reduce(run.status.cpu().numpy())),
            "conservation_rel": run.conservation(), "dt0": run.dt0}
     keep = {"base": base, "base_dev": base_dev, "gx": gx, "u0_host": u0_host}
@@ -595,7 +618,7 @@ def uniform256_record(args, native, dev, peaks, hbm_peak, flops, cpu):
            "graph": {"ms_per_step": el_graph / args.steps * 1e3,
                      "value": cells * args.steps / el_graph},
            "roofline": rl.get("alu"), "roofline_hbm": rl["hbm"], "cpu_baseline": cpu,
-           "tuned": {"ctas_per_sm": tuned["ctas_per_sm"], "candidates_ms": tuned["all"]},
+           "tuned": tuned_record(tuned),
            "conservation_rel": run.conservation()}
     u0 = None
     if not args.no_e2e:
@@ -659,8 +682,7 @@ def amr_record(args, native, dev):
                         "launch over all groups, face fluxes on",
             "groups": N, "value": cells * args.steps / el, "ms_per_step": el / args.steps * 1e3,
             "dt_level": dtl.cpu().numpy().tolist(),
-            "tuned": {"ctas_per_sm": tuned["ctas_per_sm"], "variant": tuned["variant"],
-                      "candidates_ms": tuned["all"]}}
+            "tuned": tuned_record(tuned)}
 
 
 def modes_record(args, native, dev, peaks, hbm_peak, flops, refs):
@@ -684,7 +706,7 @@ def modes_record(args, native, dev, peaks, hbm_peak, flops, refs):
         rl = rooflines(flops, cells, kms, 8 if mode == 2 else 4, peaks, hbm_peak, None, name,
                        "hydro_step_kernel (fused level)")
         rec = {"kernel_ms": kms, "value": cells / (kms / 1e3),
-               "step_value": cells * steps / el, "ctas_per_sm": tuned["ctas_per_sm"],
+               "step_value": cells * steps / el, "tuned": tuned_record(tuned),
                "roofline": rl.get("alu"), "roofline_hbm_frac": rl["hbm"]["frac"]}
         del run
         for key, (G0, dts, ref, _) in refs.items():
@@ -751,14 +773,10 @@ def main():
         # CPU baseline leg: the oracle on bounded samples of the headline and
         # config-2 workloads, its flop count, and the precision-study runs
         # whose states are the reference of the modes' rel-L1 figures
-        base = keep["base"].astype(np.float32).astype(np.float64)
-        fill = (native.gamer_fill_ghosts_uniform_f64 if args.mode == "f64"
-                else native.gamer_fill_ghosts_uniform_f32)
-        T = torch.float64 if args.mode == "f64" else torch.float32
-        d_tiles = torch.empty((4096, 5, 20, 20, 20), device=dev, dtype=T)
-        fill(keep["base_dev"], d_tiles, 16, 16, 16, 0)   # the level's distinct 20^3 inputs
-        tiles = d_tiles.double().cpu().numpy()
-        del d_tiles
+        base = keep["base"]
+        if args.mode != "f64":
+            base = base.astype(np.float32).astype(np.float64)
+        tiles = periodic_tiles(base, 16)   # the level's 4,096 distinct 20^3 inputs
         dh = 1.0 / (16 * keep["gx"])
         v, cores, desc = oracle_rate(tiles, head["dt0"], dh, args.cpu_seconds)
         flops = oracle_flops_per_cell(tiles[0], head["dt0"], dh)
@@ -768,10 +786,9 @@ def main():
         if extras:
             import oracle
             lv = uniform256_level().astype(np.float32).astype(np.float64)
-            t256 = oracle.fill_ghosts_uniform(lv, 16, 16, 16, 0)
-            v2, c2, d2 = oracle_rate(t256, 1e-3, 1 / 256, args.cpu_seconds)
+            v2, c2, d2 = oracle_rate(periodic_tiles(lv, 16), 1e-3, 1 / 256, args.cpu_seconds)
             cpu256 = {"value": v2, "unit": UNIT, "cores": c2, "kind": "oracle", "sample": d2}
-            refs["kh256_cfl0.5_100steps"] = oracle_precision_reference("kh", 256, 100, 0.5)
+            refs["kh128_cfl0.5_100steps"] = oracle_precision_reference("kh", 128, 100, 0.5)
             refs["sedov128_cfl0.3_100steps"] = oracle_precision_reference("sedov", 128, 100, 0.3)
     traffic = measured_traffic(args.mode, head["groups"])
     rl = rooflines(flops, head["cells_per_step"], head["kernel_ms"], esz, peaks, hbm_peak,

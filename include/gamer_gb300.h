@@ -489,12 +489,16 @@ const char* gamer_version(void);
  * reads it, so change it only while no other thread is launching steps. */
 int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
 
-/* Code shape of the hydro kernel: 0 = one problem at a time per thread
- * (default); 1 = as 0 with one out-of-line copy of the Riemann solver (FP32
- * 3-CTA build only); 2 = two interleaved problems per thread (z-face states in
- * shared memory, branch-free Roe path, compile-time limiter; 2 CTAs per SM in
- * FP32, 1 in FP64), all modes.  Used by the autotuner; process-wide and
- * unsynchronised like gamer_set_hydro_ctas_per_sm. */
+/* Code shape of the hydro kernel: 0 = one problem at a time per thread, 160
+ * threads per group (default); 1 = as 0 with one out-of-line copy of the
+ * Riemann solver (FP32 3-CTA tile build only); 2 = two interleaved problems per
+ * thread (z-face states in shared memory, branch-free Roe path, compile-time
+ * limiter; 2 CTAs per SM in FP32, 1 in FP64; tile path only); 3 = 320 threads
+ * per group, one owned column or face-slab cell per thread, 2 CTAs per SM
+ * (FP32-storage modes, tile and level paths).  Where a variant does not
+ * exist for a call (mode, path, HLLC or characteristic limiting) the default
+ * shape runs.  Used by the autotuner; process-wide and unsynchronised like
+ * gamer_set_hydro_ctas_per_sm. */
 int gamer_set_hydro_variant(int32_t variant);
 
 /* Debug facility (not part of the scheme): with on = 1, every later launch of

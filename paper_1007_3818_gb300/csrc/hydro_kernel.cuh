@@ -790,20 +790,22 @@ __device__ __forceinline__ bool is_read_cell(int i, int j, int k) {
 }
 
 // Plane cell of this thread's r-th conversion (r = 0, 1, 2), or -1: cell
-// tid + r * kThreads while inside the plane.
+// tid + r * NT while inside the plane (NT threads per group).
+template <int NT = kThreads>
 __device__ __forceinline__ int convert_cell(int r) {
-    const int c = int(threadIdx.x) + r * kThreads;
+    const int c = int(threadIdx.x) + r * NT;
     return c < kPlane ? c : -1;
 }
 
 // Which of this thread's plane cells (convert_cell(r), r < 3) the stencil
 // reads, for the three kinds of plane (bit 3 * kind + r): kind 0 a plane
 // inside the group, 1 one plane outside (-1, 16), 2 two outside (-2, 17).
+template <int NT = kThreads>
 __device__ __forceinline__ uint32_t read_cell_mask() {
     uint32_t m = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const int c = convert_cell(r);
+        const int c = convert_cell<NT>(r);
         if (c < 0) break;
         const int i = c % 20 - 2, j = c / 20 - 2;
         if (is_read_cell(i, j, 0)) m |= 1u << r;
@@ -821,13 +823,13 @@ __device__ __forceinline__ uint32_t plane_read_bits(uint32_t mask, int kp) {
 
 // Conserved plane -> primitive plane (all 400 cells, by convert_cell; the
 // flag covers the read cells, `rbits` from plane_read_bits).
-template <int MODE, class T, class P>
+template <int MODE, int NT = kThreads, class T, class P>
 __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W,
                                               uint32_t rbits, const KConst<T, P>& kc,
                                               uint32_t& st) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const int c = convert_cell(r);
+        const int c = convert_cell<NT>(r);
         if (c < 0) break;
         T u[5];
 #pragma unroll
@@ -918,12 +920,12 @@ struct alignas(16) GatherPlan {
                     // offset in the plane
 };
 
-// row and 16-byte chunk of the interior run of this thread
-template <class T> struct GatherRow {
+// row and 16-byte chunk of the interior run of this thread (NT threads)
+template <class T, int NT = kThreads> struct GatherRow {
     static constexpr int E16 = 16 / int(sizeof(T));  // cells per 16-byte chunk
     static constexpr int CH = 16 / E16;              // chunks per 16-cell row: 4 or 8
-    static constexpr int VS = kThreads / CH / 20;    // variables per pass: 2 or 1
-    static_assert(VS * 20 * CH == kThreads, "gather mapping");
+    static constexpr int VS = NT / CH / 20;          // variables per pass: 1, 2 or 4
+    static_assert(VS * 20 * CH == NT, "gather mapping");
     int q, v0, j;
     __device__ __forceinline__ GatherRow() {
         const int R0 = int(threadIdx.x) / CH;
@@ -933,9 +935,9 @@ template <class T> struct GatherRow {
     }
 };
 
-template <class T>
+template <class T, int NT = kThreads>
 __device__ __forceinline__ GatherPlan make_plan(const LevelGeom& L, int bx, int by) {
-    const GatherRow<T> w;
+    const GatherRow<T, NT> w;
     GatherPlan P;
     const int ny = 16 * L.gy, nx = 16 * L.gx;
     const int Y = wrap_near(by * 16 + w.j - 2, ny, L.bc);
@@ -944,7 +946,7 @@ __device__ __forceinline__ GatherPlan make_plan(const LevelGeom& L, int bx, int 
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         P.gh[r] = 0;
-        const int it = int(threadIdx.x) + r * kThreads;
+        const int it = int(threadIdx.x) + r * NT;
         if (it < 180) {
             const int v = it / 36, rem = it - 36 * v;
             const int jj = 1 + (rem >> 1), side = rem & 1;
@@ -963,11 +965,11 @@ __device__ __forceinline__ GatherPlan make_plan(const LevelGeom& L, int bx, int 
 // Gathers input plane kp of the group of plan P (z index bz) from the level
 // into its ring slot; every thread then arrives on the slot's barrier
 // (expected count kThreads).
-template <int RING, class SM, class T>
+template <int RING, int NT = kThreads, class SM, class T>
 __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
                                              const LevelGeom& L, const GatherPlan& P, int bz,
                                              int kp) {
-    using G = GatherRow<T>;
+    using G = GatherRow<T, NT>;
     const G w;
     const int slot = (kp + 2) % RING;
     T* plane = S.raw[slot] + raw_offset<1, T>();
@@ -989,7 +991,7 @@ __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
     if (dk <= 1) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            if (r == 1 && threadIdx.x >= 180 - kThreads) break;
+            if (int(threadIdx.x) + r * NT >= 180) break;
             const T* src = lz + int64_t(P.gh[r]) * 16 + ((P.bits >> (4 * r)) & 15u);
             T* dst = plane + ((P.bits >> (10 + 11 * r)) & 2047u);
             if (P.bits & (1u << (8 + r))) {
@@ -1006,8 +1008,8 @@ __device__ __forceinline__ void gather_plane(SM& S, const T* __restrict__ level,
 // Plane loaders by input kind, set up once per group: 0 -- TMA bulk copies of
 // the tile's plane issued by thread 0; 1 -- gather from the level by all
 // threads, with the plan in `plan` (kThreads entries of shared memory).
-template <int SRC, int RING, class T> struct PlaneLoader;
-template <int RING, class T> struct PlaneLoader<0, RING, T> {
+template <int SRC, int RING, class T, int NT = kThreads> struct PlaneLoader;
+template <int RING, class T, int NT> struct PlaneLoader<0, RING, T, NT> {
     static constexpr size_t kExtraSmem = 0;
     const T* gin;
     bool drop;  // debug: withhold plane 5 (LevelGeom::drop_group)
@@ -1021,8 +1023,8 @@ template <int RING, class T> struct PlaneLoader<0, RING, T> {
         return true;
     }
 };
-template <int RING, class T> struct PlaneLoader<1, RING, T> {
-    static constexpr size_t kExtraSmem = kThreads * sizeof(GatherPlan);
+template <int RING, class T, int NT> struct PlaneLoader<1, RING, T, NT> {
+    static constexpr size_t kExtraSmem = NT * sizeof(GatherPlan);
     const T* level;
     const LevelGeom& L;
     GatherPlan* plan;
@@ -1033,7 +1035,7 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
         : level(in), L(geo), plan(plan_ + threadIdx.x), drop(g == geo.drop_group) {
         const int bx = int(g % geo.gx), by = int((g / geo.gx) % geo.gy);
         bz = geo.z0 + int(g / (int64_t(geo.gx) * geo.gy));
-        *plan = make_plan<T>(geo, bx, by);  // read back by this thread only
+        *plan = make_plan<T, NT>(geo, bx, by);  // read back by this thread only
     }
     template <class SM> __device__ __forceinline__ bool load(SM& S, int kp) const {
         if (drop && kp == 5) return false;  // debug: no copy, no arrival
@@ -1042,12 +1044,12 @@ template <int RING, class T> struct PlaneLoader<1, RING, T> {
             // stencil read outside the gathered set shows up in the results
             // (the slot's previous plane was consumed before this call)
             T* slot = S.raw[(kp + 2) % RING];
-            for (int c = threadIdx.x; c < 5 * kPlane + 4; c += kThreads)
+            for (int c = threadIdx.x; c < 5 * kPlane + 4; c += NT)
                 slot[c] = __int_as_float(0x7fc00000) + T(0);
             __syncthreads();
         }
         const GatherPlan P = *plan;
-        gather_plane<RING>(S, level, L, P, bz, kp);
+        gather_plane<RING, NT>(S, level, L, P, bz, kp);
         return true;
     }
 };
@@ -1100,8 +1102,11 @@ __device__ __forceinline__ void mark_abandoned(int64_t g, int64_t N, uint32_t* s
 // limiter compiled in (1) or the limiter read from kc.limiter per slope (0).
 // RING: input planes in flight (2: the copy of plane k+2 goes out after phase A
 // of plane k; 3: plane k+3 does, one full iteration ahead of its use).
-template <int MODE, int MINB, int RSV = 0, int SRC = 0, int RING = 2>
-__global__ void __launch_bounds__(kThreads, MINB)
+// NT: threads per group, 160 (a thread owns two interior columns or one
+// column and a face-slab cell) or 320 (one column or one slab cell each: half
+// the registers per thread for twice the warps per SM).
+template <int MODE, int MINB, int RSV = 0, int SRC = 0, int RING = 2, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB)
     hydro_step_kernel(const typename Prec<MODE>::T* __restrict__ in,
                       typename Prec<MODE>::T* __restrict__ out,
                       typename Prec<MODE>::T* __restrict__ face_flux,
@@ -1110,42 +1115,49 @@ __global__ void __launch_bounds__(kThreads, MINB)
                       KConst<typename Prec<MODE>::T, typename Prec<MODE>::P> kc,
                       LevelGeom geo) {
     using T = typename Prec<MODE>::T;
+    static_assert(NT == 160 || NT == 320, "threads per group");
+    constexpr bool kWide = NT == 320;
     constexpr int kLim = (RSV & 8) ? 0 : -1;  // van Leer compiled in, or kc.limiter
     constexpr int kRec = (RSV >> 2) & 1;
     extern __shared__ __align__(128) unsigned char smem_bytes[];
     Smem<T, RING>& S = *reinterpret_cast<Smem<T, RING>*>(smem_bytes);
     constexpr int ROFF = raw_offset<SRC, T>();
     GatherPlan* gplan = reinterpret_cast<GatherPlan*>(smem_bytes + sizeof(Smem<T, RING>));
-    const uint32_t rmask = read_cell_mask();
+    const uint32_t rmask = read_cell_mask<NT>();
     const uint32_t polls = geo.wait_polls ? geo.wait_polls : kWaitPolls;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < RING; ++s) mbar_init(&S.mbar[s], SRC == 0 ? 1 : kThreads);
+        for (int s = 0; s < RING; ++s) mbar_init(&S.mbar[s], SRC == 0 ? 1 : NT);
         mbar_init_fence();
     }
     __syncthreads();
     uint32_t parity = 0;   // bit s: phase parity expected next on slot s
     uint32_t pending = 0;  // bit s: a copy into slot s was issued and not yet waited for
 
-    // owned interior columns: a warp owns a row pair (jA, jA + 4), lane -> i;
-    // warps 0-4 own pairs 0-4 (c0), warps 0-2 also pairs 5-7 (c1)
-    const bool two = tid < 96;
+    // owned interior columns: a warp owns a row pair (jA, jA + 4), lane -> i.
+    // NT 160: warps 0-4 own pairs 0-4 (c0), warps 0-2 also pairs 5-7 (c1).
+    // NT 320: warps 0-7 own pairs 0-7 (c0 only); warps 8-9 own no column
+    // (their pair index is folded into 0-7 only to keep unused indices in
+    // bounds).
+    const bool owner = kWide ? (tid < 256) : true;
+    const bool two = kWide ? false : (tid < 96);
     const int i0 = lane & 15, hb = (lane >> 4) * 4;
-    const int pa = warp, pb = warp + 5;
+    const int pa = kWide ? (warp & 7) : warp, pb = warp + 5;
     const int j0 = (pa & 3) + ((pa >> 2) << 3) + hb;
     const int j1 = (pb & 3) + ((pb >> 2) << 3) + hb;
     const int pc0 = (j0 + 2) * 20 + (i0 + 2);
     const int pc1 = (j1 + 2) * 20 + (i0 + 2);
     const int fa0 = frow(j0) * 16 + i0, fa1 = frow(j1) * 16 + i0;
-    // face-slab cell of threads 96..159: side 0: i=-1, 1: i=16, 2: j=-1, 3: j=16
-    const int sl = tid - 96, side = sl >> 4, st_ = sl & 15;
+    // face-slab cell of threads 96..159 (NT 160) or 256..319 (NT 320): side 0:
+    // i=-1, 1: i=16, 2: j=-1, 3: j=16
+    const int sl = tid - (kWide ? 256 : 96), side = sl >> 4, st_ = sl & 15;
     const int si = (side == 0) ? -1 : (side == 1) ? 16 : st_;
     const int sj = (side == 2) ? -1 : (side == 3) ? 16 : st_;
     const int psl = (sj + 2) * 20 + (si + 2);
-    // second prediction item of every thread: its second column (warps 0-2) or
-    // its slab cell (warps 3-4).  Both kinds store all four x/y faces; a slab
+    // second prediction item: the second column (NT 160, warps 0-2) or the slab
+    // cell (NT 160 warps 3-4; NT 320 warps 8-9).  Both kinds store all four x/y faces; a slab
     // cell's three unused faces go to entries 272..287 of their arrays, which
     // nothing reads, so one code path serves both.
     const int pc_b = two ? pc1 : psl;
@@ -1158,7 +1170,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
     for (int64_t g = blockIdx.x; g < N; g += gridDim.x) {
         // one input plane into its ring slot (all threads call load_plane)
-        const PlaneLoader<SRC, RING, T> loader(in, g, geo, gplan);
+        const PlaneLoader<SRC, RING, T, NT> loader(in, g, geo, gplan);
         auto load_plane = [&](int kp) { return loader.load(S, kp); };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * (kc.flux9 ? 9 : 6) * kFluxPlane : nullptr;
@@ -1182,7 +1194,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (mbar_wait(&S.mbar[0], parity & 1u, polls)) {
             parity ^= 1u;
             pending &= ~1u;
-            convert_plane<MODE>(S.raw[0] + ROFF, S.W[0], plane_read_bits(rmask, -2), kc, st);
+            convert_plane<MODE, NT>(S.raw[0] + ROFF, S.W[0], plane_read_bits(rmask, -2), kc, st);
         } else {
             timed_out = true;
         }
@@ -1194,7 +1206,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (!timed_out && mbar_wait(&S.mbar[s], (parity >> s) & 1u, polls)) {
                 parity ^= 1u << s;
                 pending &= ~(1u << s);
-                convert_plane<MODE>(S.raw[s] + ROFF, S.W[kp + 2], plane_read_bits(rmask, kp), kc,
+                convert_plane<MODE, NT>(S.raw[s] + ROFF, S.W[kp + 2], plane_read_bits(rmask, kp), kc,
                                     st);
             } else {
                 timed_out = true;
@@ -1254,7 +1266,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 if (k - 1 >= 0) {
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
-                        if (cc == 1 && !two) break;
+                        if ((cc == 0 && !owner) || (cc == 1 && !two)) break;
                         const int fa = cc ? fa1 : fa0;
                         const T* uc = cc ? uc1 : uc0;
                         T* Ec = cc ? E1 : E0;
@@ -1273,7 +1285,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 }
 
                 // ---- phase CA, part A(k): half-step prediction of plane k
-                {
+                if (owner) {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
                     T fs[6][5];
@@ -1294,7 +1306,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         zpn0[q] = fs[5][q];
                     }
                 }
-                if (two || inner) {
+                if (kWide ? (!owner && inner) : (two || inner)) {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc_b];
                     T fs[6][5];
@@ -1328,7 +1340,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     // and enters plane k
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
-                        if (cc == 1 && !two) break;
+                        if ((cc == 0 && !owner) || (cc == 1 && !two)) break;
                         const T* zp = cc ? zp1 : zp0;
                         const T* zm = cc ? zm1 : zm0;
                         const int jj = cc ? j1 : j0;
@@ -1358,9 +1370,16 @@ __global__ void __launch_bounds__(kThreads, MINB)
                 if (inner) {
                     // x faces: item = j*17 + f (f: face between i = f-1 and f)
                     // y faces: item = 272 + f*16 + i (f: face between j = f-1 and f)
-                    const int nxy = two ? 3 : 4;
+                    // NT 160: threads 0-95 take items tid + 96 r (r < 3), the
+                    // others 288 + (tid - 96) + 64 r (r < 4): five solves each
+                    // with the z face.  NT 320: owners take item tid and, for
+                    // tid < 96, 256 + tid; the slab threads 352 + (tid - 256)
+                    // + 64 r (r < 3): two or three solves per thread.
+                    const int nxy = kWide ? (owner ? (tid < 96 ? 2 : 1) : 3) : (two ? 3 : 4);
                     for (int r = 0; r < nxy; ++r) {
-                        const int it = two ? (r * 96 + tid) : (288 + r * 64 + (tid - 96));
+                        const int it = kWide ? (owner ? (r == 0 ? tid : 256 + tid)
+                                                      : (352 + (tid - 256) + 64 * r))
+                                             : (two ? (r * 96 + tid) : (288 + r * 64 + (tid - 96)));
                         const bool isy = it >= 272;
                         int lo, hi, a, b;
                         T *LA, *RA;
@@ -1425,7 +1444,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                     if (mbar_wait(&S.mbar[slot], (parity >> slot) & 1u, polls)) {
                         parity ^= 1u << slot;
                         pending &= ~(1u << slot);
-                        convert_plane<MODE>(S.raw[slot] + ROFF, S.W[(k + 4) % 3],
+                        convert_plane<MODE, NT>(S.raw[slot] + ROFF, S.W[(k + 4) % 3],
                                             plane_read_bits(rmask, k + 2), kc, st);
                     } else {
                         timed_out = true;
@@ -1459,7 +1478,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
             if (tid == 0) {
                 if (partials) {
                     double m = 0.0, s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-                    for (int w = 0; w < kThreads / 32; ++w) {
+                    for (int w = 0; w < NT / 32; ++w) {
                         m = fmax(m, red[w][0]);
                         for (int q = 0; q < 5; ++q) s[q] += red[w][1 + q];
                     }

@@ -110,6 +110,7 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     // (the fused gather adds its per-thread plans after the Smem block)
     constexpr int extra = int(PlaneLoader<SRC, 2, T>::kExtraSmem);
     int smem = int(sizeof(Smem<T, 2>)) + extra;
+    int threads = kThreads;
     // the default limiter (van Leer) is compiled into the default builds;
     // the others are read per slope from kc.limiter
     const bool vl = p->limiter == 0;
@@ -128,6 +129,14 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         if constexpr (MODE == GAMER_MODE_F32 && SRC == 0) {
             if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
         }
+        // variant 3: 320 threads per group (one column per thread), 2 CTAs
+        // per SM, three input planes in flight
+        if (var == 3) {
+            kern = vl ? hydro_step_kernel<MODE, 2, 8, SRC, 3, 320>
+                      : hydro_step_kernel<MODE, 2, 0, SRC, 3, 320>;
+            smem = int(sizeof(Smem<T, 3>)) + int(PlaneLoader<SRC, 3, T, 320>::kExtraSmem);
+            threads = 320;
+        }
     }
     if (special) {
         // Riemann solver in bits 0-1, characteristic limiting in bit 2; HLLC
@@ -144,13 +153,14 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
                    : rsv == 4 ? hydro_step_kernel<MODE, 3, 4, SRC, 2>
                               : hydro_step_kernel<MODE, 3, 6, SRC, 2>;
             smem = int(sizeof(Smem<T, 2>)) + extra;
+            threads = kThreads;
         }
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return GAMER_E_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return GAMER_E_CUDA;
@@ -167,8 +177,9 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
             cudaSuccess)
         return GAMER_E_CUDA;
     const int64_t grid = std::min<int64_t>(N, int64_t(per_sm) * dev.sm_count);
-    kern<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(in, out, face_flux, dt, dh, status,
-                                                            partials, N, kc, geo);
+    kern<<<dim3(unsigned(grid)), dim3(unsigned(threads)), smem, s>>>(in, out, face_flux, dt, dh,
+                                                                     status, partials, N, kc,
+                                                                     geo);
     return cudaGetLastError() == cudaSuccess ? GAMER_OK : GAMER_E_CUDA;
 }
 

@@ -1,13 +1,16 @@
 """Autotuner for the launch shape of the hydro step and the host pipeline.
 
-The hydro kernel's work decomposition fixes 160 threads per patch group (320
-predictions and 800 Riemann solves per plane divide evenly); what is left to
-choose per GPU and precision mode is the register / shared-memory split and
-the persistent grid:
+What is chosen per GPU, precision mode and batch size:
 
-  * variant: the build sized for 2 CTAs per SM (no register spills) or for 3
-    (more warps per SM, a few spills);
-  * CTAs per SM actually launched (1 .. the variant's limit);
+  * threads per group: 160 (a thread owns two interior columns, or one and a
+    face-slab cell; 320 predictions and 800 Riemann solves per plane divide
+    evenly) or 320 (variant 3: one column or slab cell per thread, 96
+    registers, 2 CTAs = 20 warps per SM);
+  * the register / shared-memory split of the 160-thread build: sized for 2
+    CTAs per SM (no register spills, three input planes in flight) or for 3
+    (more warps per SM, two planes in flight);
+  * on the tile path also the Riemann solver out of line (variant 1) and the
+    two-problems-per-thread pair kernel (variant 2);
   * for the streamed host pipeline, the batch size in groups.
 
 Each candidate is timed with CUDA events on a batch of the caller's shape and
@@ -60,13 +63,15 @@ def tune_hydro(mode, inp, out, face_flux, dt, dh, status, partials, params, reps
         native.gamer_set_hydro_variant(_cache[key]["variant"])
         return _cache[key]
     # (CTAs per SM, code variant): the FP32 3-CTA build also comes with the
-    # Riemann solver out of line (smaller code for the instruction cache)
+    # Riemann solver out of line (smaller code for the instruction cache);
+    # every mode has the pair kernel, the FP32-storage modes the 320-thread
+    # build
     if mode == native.GAMER_MODE_F64:
-        candidates = [(1, 0)]
+        candidates = [(1, 0), (0, 2)]
     elif mode == native.GAMER_MODE_F32:
-        candidates = [(2, 0), (3, 0), (3, 1)]
+        candidates = [(2, 0), (3, 0), (3, 1), (0, 2), (0, 3)]
     else:
-        candidates = [(2, 0), (3, 0)]
+        candidates = [(2, 0), (3, 0), (0, 2), (0, 3)]
     results = {}
     for c, v in candidates:
         native.gamer_set_hydro_ctas_per_sm(mode, c)
@@ -76,7 +81,8 @@ def tune_hydro(mode, inp, out, face_flux, dt, dh, status, partials, params, reps
     best = min(results, key=results.get)
     native.gamer_set_hydro_ctas_per_sm(mode, best[0])
     native.gamer_set_hydro_variant(best[1])
-    res = {"ctas_per_sm": best[0], "variant": best[1], "ms": results[best],
+    res = {"ctas_per_sm": best[0], "variant": best[1],
+           "threads_per_group": 320 if best[1] == 3 else 160, "ms": results[best],
            "all": {f"{c}x{v}": t for (c, v), t in results.items()}}
     _cache[key] = res
     if cache_path:
@@ -126,18 +132,22 @@ def tune_hydro_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status
     key = ("level", torch.cuda.get_device_name(), int(mode), _bucket(gx * gy * gz))
     if key in _cache:
         native.gamer_set_hydro_ctas_per_sm(mode, _cache[key]["ctas_per_sm"])
-        native.gamer_set_hydro_variant(0)
+        native.gamer_set_hydro_variant(_cache[key]["variant"])
         return _cache[key]
-    candidates = [1] if mode == native.GAMER_MODE_F64 else [2, 3]
-    native.gamer_set_hydro_variant(0)
+    # (CTAs per SM, variant): the 160-thread builds for 2 and 3 CTAs per SM,
+    # and the 320-thread build (FP32-storage modes)
+    candidates = [(1, 0)] if mode == native.GAMER_MODE_F64 else [(2, 0), (3, 0), (0, 3)]
     results = {}
-    for c in candidates:
+    for c, v in candidates:
         native.gamer_set_hydro_ctas_per_sm(mode, c)
-        results[c] = _time(lambda: native.hydro_advance_level(
+        native.gamer_set_hydro_variant(v)
+        results[(c, v)] = _time(lambda: native.hydro_advance_level(
             mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status, partials, params), reps)
     best = min(results, key=results.get)
-    native.gamer_set_hydro_ctas_per_sm(mode, best)
-    res = {"ctas_per_sm": best, "variant": 0, "ms": results[best],
-           "all": {str(c): t for c, t in results.items()}}
+    native.gamer_set_hydro_ctas_per_sm(mode, best[0])
+    native.gamer_set_hydro_variant(best[1])
+    res = {"ctas_per_sm": best[0], "variant": best[1],
+           "threads_per_group": 320 if best[1] == 3 else 160, "ms": results[best],
+           "all": {f"{c}x{v}": t for (c, v), t in results.items()}}
     _cache[key] = res
     return res

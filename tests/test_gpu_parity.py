@@ -291,7 +291,8 @@ def test_sod_single_group_ten_steps(mode):
 # meet the same parity bar.
 VARIANTS = [pytest.param(F32, 0, id="f32-v0"), pytest.param(F32, 1, id="f32-v1"),
             pytest.param(F32, 2, id="f32-v2"), pytest.param(MIXED, 2, id="mixed-v2"),
-            pytest.param(F64, 2, id="f64-v2")]
+            pytest.param(F64, 2, id="f64-v2"), pytest.param(F32, 3, id="f32-v3"),
+            pytest.param(MIXED, 3, id="mixed-v3"), pytest.param(FF, 3, id="ff-v3")]
 
 
 @pytest.fixture
@@ -299,7 +300,7 @@ def variant_guard():
     from paper_1007_3818_gb300 import native
     yield native
     native.gamer_set_hydro_variant(0)
-    for m in (F32, MIXED, F64):
+    for m in (F32, MIXED, F64, FF):
         native.gamer_set_hydro_ctas_per_sm(m, 0)
 
 
@@ -510,6 +511,26 @@ def test_fused_level_launch_shapes(variant_guard, mode, ctas, bc, dims):
     ring, 3 CTAs with a 2-plane ring) gather the level correctly."""
     variant_guard.gamer_set_hydro_ctas_per_sm(mode, ctas)
     _fused_vs_fill(mode, bc, dims)
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED, FF], ids=["f32", "mixed", "ff"])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1), (4, 1, 2)])
+def test_fused_level_320_threads_per_group(variant_guard, mode, bc, dims):
+    """The 320-thread build (variant 3: one owned column or face-slab cell per
+    thread, its own gather mapping) on the level and tile paths: bit for bit
+    equal to each other, element-wise equal to the oracle."""
+    variant_guard.gamer_set_hydro_variant(3)
+    _fused_vs_fill(mode, bc, dims)
+
+
+def test_fused_level_320_threads_with_poisoned_slots(variant_guard, poison_guard):
+    """The 320-thread gather copies every cell the stencil reads (slots
+    NaN-filled before each gather)."""
+    variant_guard.gamer_set_hydro_variant(3)
+    for mode in (F32, FF):
+        for bc in (0, 1):
+            _fused_vs_fill(mode, bc, (3, 2, 4))
 
 
 def _fused_vs_fill(mode, bc, dims):
