@@ -84,6 +84,7 @@ struct alignas(16) Smem {
     T xm[5 * kFaceStride], xp[5 * kFaceStride], ym[5 * kFaceStride], yp[5 * kFaceStride];
     uint64_t mbar[RING];
     uint32_t status;
+    T lam;  // dt / dh of the group being advanced (rounded once from FP64 by thread 0)
 };
 
 template <class T, class P>
@@ -113,16 +114,19 @@ constexpr int kFluxPlane = 5 * 256;  // one plane: [5][16][16]
 
 // ---------------------------------------------------------------------------
 // Selective FP64 in the mixed mode.  The pressure p = (gamma - 1)(E - ke),
-// ke = |m|^2 / (2 rho), is recovered in FP32 with gamma - 1 held as a
-// (hi, lo) float pair, so no systematic bias from rounding gamma - 1 enters;
-// its relative error is then at most about (2 + 6 r / (1 - r)) u, r = ke / E,
-// u = 2^-24 (ke carries ~6 roundings, rcp.approx included, and the
-// subtraction magnifies them by ke / (E - ke)).  Where the kinetic energy is
-// more than half the total (r > 1/2: the flow is supersonic to within a
-// factor of order one) that bound passes 8 u and grows without limit as
-// E - ke cancels, so there p is recovered in FP64 instead: 1/rho from the
-// FP32 seed plus one Newton step, E - ke in FP64, one rounding.  Below the
-// threshold the FP32 result is within a few ulps of the FP64 one.
+// ke = |m|^2 / (2 rho), is recovered in FP32 as gm1 E - gm1 ke + gm1_lo (E -
+// ke), with gamma - 1 held as the float pair (gm1, gm1_lo): the product with
+// E is exact inside the final FMA, so E - ke is never rounded before it is
+// scaled and no rounding bias of gamma - 1 enters.  Its relative error is
+// about u + 8 u r / (1 - r), r = ke / E, u = 2^-24 (ke and gm1 ke carry some
+// eight roundings, rcp.approx included, each magnified by ke / (E - ke)):
+// below one ulp for small r, 9 u at r = 1/2, unbounded as E - ke cancels.
+// Where the kinetic energy is more than half the total (r > 1/2: the flow is
+// supersonic to within a factor of order one) p is recovered in FP64
+// instead: 1/rho from the FP32 seed plus one Newton step, E - ke in FP64, one
+// rounding.  In the Riemann solves and the half-step admissibility tests the
+// FP32 path runs for every state and one rarely taken branch per solve or
+// per predicted cell redoes it exactly when any of its states needs FP64.
 constexpr float kMixedKeFraction = 0.5f;
 
 static __device__ __noinline__ float pressure_fp64(float r, float m1, float m2, float m3, float E,
@@ -135,10 +139,25 @@ static __device__ __noinline__ float pressure_fp64(float r, float m1, float m2, 
     return static_cast<float>(gm1p * (static_cast<double>(E) - ke));
 }
 
-// rho E - |m|^2 / 2 > 0 in FP64 (the undecided cases of admissible<MIXED>)
-static __device__ __noinline__ bool positive_fp64(float r, float m1, float m2, float m3, float E) {
-    const double a = m1, b = m2, c = m3;
-    return (double(r) * double(E) - 0.5 * (a * a + b * b + c * c)) > 0.0;
+// rho > 0 and rho E - |m|^2 / 2 > 0 of six conserved states, the difference
+// in FP64 (a predicted cell whose FP32 tests were not all certain)
+struct States6 {
+    float v[6][5];
+};
+static __device__ __noinline__ bool admissible6_fp64(States6 f) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double a = f.v[i][1], b = f.v[i][2], c = f.v[i][3];
+        ok &= (f.v[i][0] > 0.0f) &
+              ((double(f.v[i][0]) * double(f.v[i][4]) - 0.5 * (a * a + b * b + c * c)) > 0.0);
+    }
+    return ok;
+}
+
+// The mixed mode's FP32 recovery from E and ke (see above).
+__device__ __forceinline__ float p_mixed32(float E, float ke, float gm1, float gm1_lo) {
+    return fmaf(gm1, E, fmaf(gm1_lo, E - ke, -(gm1 * ke)));
 }
 
 // Pressure from a conserved state, given 1/rho in T.  MIXED: the selective
@@ -148,8 +167,7 @@ __device__ __forceinline__ T pressure(T r, T m1, T m2, T m3, T E, T ir, const KC
     if constexpr (MODE == GAMER_MODE_MIXED) {
         const float ke = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3) * ir;
         if (ke > kMixedKeFraction * E) return pressure_fp64(r, m1, m2, m3, E, ir, kc.gm1p);
-        const float d = E - ke;
-        return fmaf(kc.gm1, d, kc.gm1_lo * d);
+        return p_mixed32(E, ke, kc.gm1, kc.gm1_lo);
     } else if constexpr (MODE == GAMER_MODE_FF) {
         // the same recovery in float-float: 1/rho = ir (1 + d), d = 1 - rho ir
         // from one FMA; |m|^2 ir exactly as p + pe; E - ke by TwoSum
@@ -211,14 +229,16 @@ __device__ __forceinline__ void apply_floors(T o[5], T& ir, T& p, const KConst<T
 // carries an error below 4 u (|rho E| + |m|^2 / 2), so where |d| exceeds
 // 2^-20 (|rho E| + |m|^2 / 2) its sign is the FP64 sign; only the cases
 // closer to zero are decided in FP64.
+// MIXED raises `und` where the FP32 sign is not certain; the caller then
+// decides in FP64 (admissible6_fp64).
 template <int MODE, class T>
-__device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E) {
+__device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E, bool& und) {
     if constexpr (MODE == GAMER_MODE_MIXED) {
         const float h = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3);
         const float re = r * E;
         const float d = re - h;
-        if (fabsf(d) > 0x1p-20f * (fabsf(re) + h)) return (r > 0.0f) & (d > 0.0f);
-        return (r > 0.0f) & positive_fp64(r, m1, m2, m3, E);
+        und |= !(fabsf(d) > 0x1p-20f * (fabsf(re) + h));
+        return (r > 0.0f) & (d > 0.0f);
     } else if constexpr (MODE == GAMER_MODE_FF) {
         float se, ee, t;
         const float s = sq3_ff(m1, m2, m3, se);
@@ -349,12 +369,23 @@ struct RoeIO {
 __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
 template <int MODE, class P>
 __device__ __forceinline__ float2 pressure_x2(float2 r, float2 m, float2 ma, float2 mb, float2 E,
-                                              float2 ir, const KConst<float, P>& kc) {
+                                              float2 ir, const KConst<float, P>& kc, bool& hi) {
     if constexpr (MODE == GAMER_MODE_F32) {
         float2 s = __fmul2_rn(m, m);
         s = __ffma2_rn(ma, ma, s);
         s = __ffma2_rn(mb, mb, s);
         return __fmul2_rn(pk(kc.gm1, kc.gm1), __ffma2_rn(__fmul2_rn(s, ir), pk(-0.5f, -0.5f), E));
+    } else if constexpr (MODE == GAMER_MODE_MIXED) {
+        // the FP32 recovery of both lanes; hi marks a lane that needs FP64
+        float2 s = __fmul2_rn(m, m);
+        s = __ffma2_rn(ma, ma, s);
+        s = __ffma2_rn(mb, mb, s);
+        const float2 ke = __fmul2_rn(__fmul2_rn(s, ir), pk(0.5f, 0.5f));
+        hi |= (ke.x > kMixedKeFraction * E.x) | (ke.y > kMixedKeFraction * E.y);
+        const float2 gk = __fmul2_rn(pk(kc.gm1, kc.gm1), ke);
+        const float2 t = __ffma2_rn(pk(kc.gm1_lo, kc.gm1_lo), __fadd2_rn(E, pk(-ke.x, -ke.y)),
+                                    pk(-gk.x, -gk.y));
+        return __ffma2_rn(pk(kc.gm1, kc.gm1), E, t);
     } else {
         return pk(pressure<MODE>(r.x, m.x, ma.x, mb.x, E.x, ir.x, kc),
                   pressure<MODE>(r.y, m.y, ma.y, mb.y, E.y, ir.y, kc));
@@ -368,7 +399,8 @@ __device__ __forceinline__ bool roe_main_x2(const float L[5], const float R[5],
     const float2 ir = pk(rcp_(L[0]), rcp_(R[0]));
     const float2 u = __fmul2_rn(m, ir), v = __fmul2_rn(ma, ir), w = __fmul2_rn(mb, ir);
     const float2 ga2 = pk(kc.gamma, kc.gamma);
-    const float2 p = pressure_x2<MODE>(r, m, ma, mb, E, ir, kc);
+    bool hi = false;  // MIXED: a state needs the FP64 recovery
+    const float2 p = pressure_x2<MODE>(r, m, ma, mb, E, ir, kc, hi);
     const float2 Ep = __fadd2_rn(E, p);
     const float2 H = __fmul2_rn(Ep, ir);
     const float2 c2 = __fmul2_rn(__fmul2_rn(ga2, p), ir);
@@ -400,9 +432,9 @@ __device__ __forceinline__ bool roe_main_x2(const float L[5], const float R[5],
     const float2 sb = __ffma2_rn(A, pk(wT, wT), mb);
     const float2 sE = __ffma2_rn(A, pk(K1E, K5E), E);
     const float2 is = pk(rcp_(sr.x), rcp_(sr.y));
-    const float2 ps = pressure_x2<MODE>(sr, sn, sa, sb, sE, is, kc);
+    const float2 ps = pressure_x2<MODE>(sr, sn, sa, sb, sE, is, kc, hi);
     const bool fallback =
-        !((cT2 > 0.0f) & (sr.x > 0.0f) & (ps.x > 0.0f) & (sr.y > 0.0f) & (ps.y > 0.0f));
+        !((cT2 > 0.0f) & (sr.x > 0.0f) & (ps.x > 0.0f) & (sr.y > 0.0f) & (ps.y > 0.0f)) | hi;
     const float2 un = __fmul2_rn(sn, is);
     const float2 cs2 = __fmul2_rn(__fmul2_rn(ga2, ps), is);
     const float l1s = un.x - sqrt_(cs2.x);
@@ -489,13 +521,43 @@ __device__ __forceinline__ void hlle_apply(const T L[5], const T R[5], const KCo
 // used): the branch-free solve, then one rarely taken branch into the single
 // out-of-line HLLE copy (measured faster than an inline fallback per call
 // site, which adds spills).
+// MIXED: the Roe flux of a face whose FP32 solve could not stand -- a state
+// needs the FP64 pressure recovery, or the HLLE fallback applies -- redone
+// with the selective scalar recovery (one out-of-line copy, rarely run).
+template <int MODE, class T, class P>
+__device__ __noinline__ RoeIO<T> roe_exact(RoeIO<T> Li, RoeIO<T> Ri, KConst<T, P> kc) {
+    RoeIO<T> out;
+    out.st = 0;
+    if (roe_main<MODE>(Li.v, Ri.v, kc, out.v)) {
+        hlle_core<MODE>(Li.v, Ri.v, kc, out.v);
+        out.st = GAMER_ST_HLLE_FALLBACK;
+    }
+    return out;
+}
+
 template <int MODE, class T, class P>
 __device__ __forceinline__ void roe_rot(const T L[5], const T R[5], const KConst<T, P>& kc,
                                         T F[5], uint32_t& st) {
     bool fb;
     if constexpr (sizeof(T) == 4) fb = roe_main_x2<MODE>(L, R, kc, F);  // FP32 storage
     else fb = roe_main<MODE>(L, R, kc, F);
-    if (fb) hlle_apply<MODE>(L, R, kc, F, st);
+    if (fb) {
+        if constexpr (MODE == GAMER_MODE_MIXED) {
+            RoeIO<T> a, b;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                a.v[q] = L[q];
+                b.v[q] = R[q];
+            }
+            a.st = b.st = 0;
+            const RoeIO<T> r = roe_exact<MODE>(a, b, kc);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) F[q] = r.v[q];
+            st |= r.st;
+        } else {
+            hlle_apply<MODE>(L, R, kc, F, st);
+        }
+    }
 }
 
 // Out-of-line form of roe_rot (one copy of the solver in the kernel's code):
@@ -745,12 +807,22 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
-    bool ok = true;
+    bool ok = true, und = false;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
-        ok &= admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4]);
+        ok &= admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4], und);
+    }
+    if constexpr (MODE == GAMER_MODE_MIXED) {
+        if (und) {
+            States6 f6;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) f6.v[f][q] = fs[f][q];
+            ok = admissible6_fp64(f6);
+        }
     }
     return ok;
 }
@@ -1174,11 +1246,12 @@ __global__ void __launch_bounds__(NT, MINB)
         auto load_plane = [&](int kp) { return loader.load(S, kp); };
         T* gout = out + g * 20480;
         T* gff = face_flux ? face_flux + g * (kc.flux9 ? 9 : 6) * kFluxPlane : nullptr;
-        const double dtg = dt[g], dhg = dh[g];
-        const T lam = static_cast<T>(dtg / dhg);
-        const T half_lam = T(0.5) * lam;
         uint32_t st = 0;
         if (tid == 0) {
+            // one FP64 division per group, shared through shared memory (read
+            // after the prologue's first barrier)
+            const double dtg = dt[g], dhg = dh[g];
+            S.lam = static_cast<T>(dtg / dhg);
             S.status = 0;
             if (!(isfinite(dtg) && isfinite(dhg) && dtg >= 0.0 && dhg > 0.0))
                 st |= GAMER_ST_BAD_INPUT;
@@ -1215,6 +1288,8 @@ __global__ void __launch_bounds__(NT, MINB)
         if (__syncthreads_or(timed_out)) goto abort_group;
 
         {
+            const T lam = S.lam;
+            const T half_lam = T(0.5) * lam;
             // owner registers: z+ state of the previous plane, the flux of the
             // z face below it, and E = U - lam (x/y flux divergence) of it
             T zp0[5], zp1[5], fzo0[5], fzo1[5], E0[5], E1[5];
@@ -1453,16 +1528,43 @@ __global__ void __launch_bounds__(NT, MINB)
                 if (__syncthreads_or(timed_out)) goto abort_group;
             }
 
-            // ---- group epilogue: reductions in FP64 across threads
-            double dmax = double(smax);
-            double dsum[5];
+            // ---- group epilogue: reductions across the warp (FP32 modes: the
+            // compensated float pairs by double-float additions, so no FP64
+            // instruction per thread), then in FP64 across warps
+            double dmax, dsum[5];
+            if constexpr (sizeof(T) == 4) {
+                float m = smax, h[5], l[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) dsum[q] = sums.get(q);
+                for (int q = 0; q < 5; ++q) {
+                    h[q] = sums.hi[q];
+                    l[q] = sums.lo[q];
+                }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+                for (int off = 16; off > 0; off >>= 1) {
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
 #pragma unroll
-                for (int q = 0; q < 5; ++q) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], off);
+                    for (int q = 0; q < 5; ++q) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, h[q], off);
+                        const float ol = __shfl_xor_sync(0xffffffffu, l[q], off);
+                        float e;
+                        h[q] = two_sum(h[q], oh, e);
+                        l[q] = (l[q] + ol) + e;
+                    }
+                }
+                dmax = double(m);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) dsum[q] = double(h[q]) + double(l[q]);
+            } else {
+                dmax = double(smax);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) dsum[q] = sums.get(q);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], off);
+                }
             }
             const uint32_t wst = __reduce_or_sync(0xffffffffu, st);
             // per-warp partials in the x- face array (no face state is live

@@ -135,6 +135,7 @@ def elementwise_excess(a, b, mode, state=True):
 
 def assert_elementwise(a, b, mode, what, state=True):
     r, idx, av, bv = elementwise_excess(a, b, mode, state)
+    print(f"element-wise excess mode {mode} {what}: {r:.3g}")
     assert r <= 1.0, (f"{what}: value {idx} (group, field, ...) is {av!r}, oracle {bv!r}: "
                       f"{r:.3g} x the element-wise bound")
     return r
