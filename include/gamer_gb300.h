@@ -131,7 +131,8 @@ typedef struct gh_params {
  * does the same recoveries (and the rho E - |m|^2/2 > 0 tests) in float-float
  * FP32 arithmetic: |m|^2 exact by FMA products and TwoSum, 1/rho refined to
  * about 2^-46, E - |m|^2/(2 rho) by TwoSum -- as accurate as the FP64 recovery
- * for FP32 states while |m|^2/(2 rho) < 2^22 p, at FP32 speed.
+ * for FP32 states while |m|^2/(2 rho) < 2^22 p, at FP32 speed (a test whose
+ * FP32 sign is certain is decided in FP32, with the same outcome).
  */
 int gamer_hydro_advance_f32(const float* in, float* out, float* face_flux, const double* dt,
                             const double* dh, uint32_t* status, double* partials, int64_t N,

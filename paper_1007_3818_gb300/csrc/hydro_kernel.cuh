@@ -155,6 +155,21 @@ static __device__ __noinline__ bool admissible6_fp64(States6 f) {
     return ok;
 }
 
+// the same in float-float (the FF mode): |m|^2 and rho E as exact pairs,
+// their difference by TwoSum
+static __device__ __noinline__ bool admissible6_ff(States6 f) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float se, ee, t;
+        const float s = sq3_ff(f.v[i][1], f.v[i][2], f.v[i][3], se);
+        const float re = two_prod(f.v[i][0], f.v[i][4], ee);
+        const float d = two_sum(re, -0.5f * s, t);
+        ok &= (f.v[i][0] > 0.0f) & ((d + ((ee - 0.5f * se) + t)) > 0.0f);
+    }
+    return ok;
+}
+
 // The mixed mode's FP32 recovery from E and ke (see above).
 __device__ __forceinline__ float p_mixed32(float E, float ke, float gm1, float gm1_lo) {
     return fmaf(gm1, E, fmaf(gm1_lo, E - ke, -(gm1 * ke)));
@@ -229,22 +244,17 @@ __device__ __forceinline__ void apply_floors(T o[5], T& ir, T& p, const KConst<T
 // carries an error below 4 u (|rho E| + |m|^2 / 2), so where |d| exceeds
 // 2^-20 (|rho E| + |m|^2 / 2) its sign is the FP64 sign; only the cases
 // closer to zero are decided in FP64.
-// MIXED raises `und` where the FP32 sign is not certain; the caller then
-// decides in FP64 (admissible6_fp64).
+// MIXED and FF take the FP32 decision where its sign is certain and raise
+// `und` elsewhere; the caller then decides those cells exactly
+// (admissible6_exact: FP64, or float-float in FF).
 template <int MODE, class T>
 __device__ __forceinline__ bool admissible(T r, T m1, T m2, T m3, T E, bool& und) {
-    if constexpr (MODE == GAMER_MODE_MIXED) {
+    if constexpr (MODE == GAMER_MODE_MIXED || MODE == GAMER_MODE_FF) {
         const float h = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3);
         const float re = r * E;
         const float d = re - h;
         und |= !(fabsf(d) > 0x1p-20f * (fabsf(re) + h));
         return (r > 0.0f) & (d > 0.0f);
-    } else if constexpr (MODE == GAMER_MODE_FF) {
-        float se, ee, t;
-        const float s = sq3_ff(m1, m2, m3, se);
-        const float re = two_prod(r, E, ee);
-        const float d = two_sum(re, -0.5f * s, t);
-        return (r > 0.0f) & ((d + ((ee - 0.5f * se) + t)) > 0.0f);
     } else {
         return (r > T(0)) & ((r * E - T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3)) > T(0));
     }
@@ -814,14 +824,14 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
         for (int q = 0; q < 5; ++q) fs[f][q] = fs[f][q] + du[q];
         ok &= admissible<MODE>(fs[f][0], fs[f][1], fs[f][2], fs[f][3], fs[f][4], und);
     }
-    if constexpr (MODE == GAMER_MODE_MIXED) {
+    if constexpr (MODE == GAMER_MODE_MIXED || MODE == GAMER_MODE_FF) {
         if (und) {
             States6 f6;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
 #pragma unroll
                 for (int q = 0; q < 5; ++q) f6.v[f][q] = fs[f][q];
-            ok = admissible6_fp64(f6);
+            ok = (MODE == GAMER_MODE_MIXED) ? admissible6_fp64(f6) : admissible6_ff(f6);
         }
     }
     return ok;
@@ -1476,40 +1486,42 @@ __global__ void __launch_bounds__(NT, MINB)
                             a = i;
                             b = f;
                         }
-                        // rotation: x -> (0,1,2,3,4); y -> (0,2,3,1,4)
-                        const int c1 = isy ? 2 : 1, c2 = isy ? 3 : 2, c3 = isy ? 1 : 3;
-                        T L[5], R[5], F[5];
-                        L[0] = LA[lo];
-                        L[1] = LA[c1 * kFaceStride + lo];
-                        L[2] = LA[c2 * kFaceStride + lo];
-                        L[3] = LA[c3 * kFaceStride + lo];
-                        L[4] = LA[4 * kFaceStride + lo];
-                        R[0] = RA[hi];
-                        R[1] = RA[c1 * kFaceStride + hi];
-                        R[2] = RA[c2 * kFaceStride + hi];
-                        R[3] = RA[c3 * kFaceStride + hi];
-                        R[4] = RA[4 * kFaceStride + hi];
+                        // rotation: x -> (0,1,2,3,4); y -> (0,2,3,1,4).  The five
+                        // components are loaded and stored at fixed offsets and
+                        // permuted in registers (three selects each way), so no
+                        // access needs a run-time component offset.
+                        T A[5], B[5], L[5], R[5], F[5];
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            A[q] = LA[q * kFaceStride + lo];
+                            B[q] = RA[q * kFaceStride + hi];
+                        }
+                        L[0] = A[0];
+                        L[1] = isy ? A[2] : A[1];
+                        L[2] = isy ? A[3] : A[2];
+                        L[3] = isy ? A[1] : A[3];
+                        L[4] = A[4];
+                        R[0] = B[0];
+                        R[1] = isy ? B[2] : B[1];
+                        R[2] = isy ? B[3] : B[2];
+                        R[3] = isy ? B[1] : B[3];
+                        R[4] = B[4];
                         roe_solve<MODE, (RSV & 3)>(L, R, kc, F, st);
-                        // the flux into the two state slots this solve consumed
-                        LA[lo] = F[0];
-                        LA[c1 * kFaceStride + lo] = F[1];
-                        LA[c2 * kFaceStride + lo] = F[2];
-                        LA[c3 * kFaceStride + lo] = F[3];
-                        LA[4 * kFaceStride + lo] = F[4];
-                        RA[hi] = F[0];
-                        RA[c1 * kFaceStride + hi] = F[1];
-                        RA[c2 * kFaceStride + hi] = F[2];
-                        RA[c3 * kFaceStride + hi] = F[3];
-                        RA[4 * kFaceStride + hi] = F[4];
+                        // the flux, back in (rho, mx, my, mz, E) order, into the two
+                        // state slots this solve consumed
+                        const T G[5] = {F[0], isy ? F[3] : F[1], isy ? F[1] : F[2],
+                                        isy ? F[2] : F[3], F[4]};
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            LA[q * kFaceStride + lo] = G[q];
+                            RA[q * kFaceStride + hi] = G[q];
+                        }
                         const int face = flux_plane(isy ? 1 : 0, b, kc.flux9);
                         if (gff && face >= 0) {
                             // x planes: [v][k][j];  y planes: [v][k][i]
                             T* dst = gff + face * kFluxPlane + k * 16 + a;
-                            dst[0] = F[0];
-                            dst[c1 * 256] = F[1];
-                            dst[c2 * 256] = F[2];
-                            dst[c3 * 256] = F[3];
-                            dst[4 * 256] = F[4];
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) dst[q * 256] = G[q];
                         }
                     }
                 }

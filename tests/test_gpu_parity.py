@@ -710,7 +710,8 @@ def test_selective_fp64_recovery_takes_both_branches_in_one_tile():
     mf, ff_, sf, _ = gpu_advance(host, dt, 1 / 16, g, FF)
     assert np.array_equal(sx, sf)
     from gpu_util import elementwise_excess
-    ex_state = elementwise_excess(mx, mf, FF)[0] * 256 / 16      # in units of 16 eps
-    ex_flux = elementwise_excess(fx, ff_, FF, state=False)[0] * 256 / 16
+    from gpu_util import ELEM_C_F32
+    ex_state = elementwise_excess(mx, mf, FF)[0] * ELEM_C_F32 / 16   # in units of 16 eps
+    ex_flux = elementwise_excess(fx, ff_, FF, state=False)[0] * ELEM_C_F32 / 16
     print(f"mixed vs float-float: {ex_state:.3g} / {ex_flux:.3g} x (16 eps (|b| + S))")
     assert ex_state <= 1.0 and ex_flux <= 1.0
