@@ -69,7 +69,8 @@ KERNEL_SOURCES = ["paper_1007_3818_gb300/csrc/hydro_kernel.cuh",
                   "paper_1007_3818_gb300/csrc/device_util.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_launch.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_f32.cu"]
-NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "bytes": None, "sources_sha256": None}
+NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "bytes": 359712768 + 434654720,
+               "sources_sha256": "f9309340824f961b45b25fb9efd7007c22e2fe442771329618b1b1cd05531705"}
 
 
 def kernel_sources_sha256():
@@ -515,6 +516,30 @@ def headline(args, native, dist, dev, world, rank):
     return rec, keep
 
 
+def link_peak(h_lv, dev):
+    """Host-link bandwidth each way with both directions busy: up to 4 GB of
+    the first host level copied in while as much of the second is copied out,
+    on two streams (GB/s, the slower direction)."""
+    import torch
+    n = min(h_lv[0].numel(), (4 << 30) // h_lv[0].element_size())
+    src, dst = h_lv[0].view(-1)[:n], h_lv[1].view(-1)[:n]
+    d_in = torch.empty(n, dtype=h_lv[0].dtype, device=dev)
+    d_out = torch.zeros(n, dtype=h_lv[0].dtype, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            d_in.copy_(src, non_blocking=True)
+        with torch.cuda.stream(s2):
+            dst.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, n * h_lv[0].element_size() / (time.perf_counter() - t0) / 1e9)
+    del d_in, d_out
+    return best
+
+
 def host_room(world, level_bytes):
     """Whether the host's available memory holds two copies of a level per
     rank with 20 % to spare."""
@@ -583,6 +608,7 @@ def end_to_end(args, native, dist, dev, world, keep, dt0):
             trial[nl] = time.perf_counter() - t0
             pl.close()
         batch = min(trial, key=trial.get) * layer
+    link = link_peak(h_lv, dev)
     pipe = native.Pipeline(mode, batch, with_flux=False)
     pipe.set_timeout(600.0)
     pipe.level_run_host(h_lv[0], h_lv[1], gx, gx, gx, 0, 1, dt0, dh, CFL, params)  # allocation
@@ -597,7 +623,12 @@ def end_to_end(args, native, dist, dev, world, keep, dt0):
     for owner in (first[1], second[1]):
         if owner is not None:
             owner.close()
+    each_way = max(h2d, d2h) / n_e2e / (el / n_e2e) / 1e9
     return {"value": world * G * GROUP_CELLS * n_e2e / el, "unit": UNIT,
+            "roofline": {"bound": "host link", "achieved": each_way, "peak": link,
+                         "unit": "GB/s each way", "frac": each_way / link,
+                         "peak_basis": "measured in this run: the same host levels copied "
+                                       "in and out at once on two streams"},
             "host_memory": ("gamer_host_alloc (huge-page backed, page-locked)"
                             if args.host_alloc == "library" else "torch pinned (cudaHostAlloc)"),
             "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
