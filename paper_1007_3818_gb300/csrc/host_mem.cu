@@ -64,12 +64,18 @@ extern "C" int gamer_host_alloc(size_t bytes, int32_t nthreads, void** out) {
     int nt = nthreads > 0 ? nthreads : int(std::thread::hardware_concurrency());
     nt = std::max(1, std::min(nt, 64));
     const size_t chunk = (len / hp + nt - 1) / nt * hp;
+    // (no exception may cross the C ABI: where a thread cannot be started,
+    // the calling thread touches that chunk itself)
     std::vector<std::thread> th;
     for (int t = 0; t < nt; ++t) {
         const size_t lo = size_t(t) * chunk;
         if (lo >= len) break;
         const size_t n = std::min(chunk, len - lo);
-        th.emplace_back([p, lo, n] { std::memset(p + lo, 0, n); });
+        try {
+            th.emplace_back([p, lo, n] { std::memset(p + lo, 0, n); });
+        } catch (...) {
+            std::memset(p + lo, 0, n);
+        }
     }
     for (auto& x : th) x.join();
     if (cudaHostRegister(p, len, cudaHostRegisterDefault) != cudaSuccess) {
@@ -77,9 +83,13 @@ extern "C" int gamer_host_alloc(size_t bytes, int32_t nthreads, void** out) {
         munmap(base, len + hp);
         return GAMER_E_CUDA;
     }
-    {
+    try {
         std::lock_guard<std::mutex> lock(g_mu);
         g_maps[p] = Mapping{base, len + hp};
+    } catch (...) {
+        cudaHostUnregister(p);
+        munmap(base, len + hp);
+        return GAMER_E_CUDA;
     }
     *out = p;
     return GAMER_OK;
