@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32_1, TOL_F64, host_input, rel_l1_fields
+from gpu_util import TOL_F32_1, TOL_F64, assert_elementwise, host_input, rel_l1_fields
 from paper_1007_3818_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -151,6 +151,8 @@ def test_nine_plane_flux_layout(mode, tol):
     _, r9, _, _ = oracle.advance_groups(tiles, 2e-3, 1 / 256, gamma=G, flux_layout=1)
     assert np.isfinite(a9).all()
     assert rel_l1_fields(a9.reshape(N * 9, 5, -1), r9.reshape(N * 9, 5, -1)) <= 10 * tol
+    # value by value too, the interior planes (x8, y8, z8) included
+    assert_elementwise(a9, r9, mode, "nine-plane face flux", state=False)
 
 
 @pytest.mark.parametrize("mode,tol", [(F32, 2e-6), (F64, 1e-13)], ids=["f32", "f64"])
