@@ -496,8 +496,6 @@ int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
  * thread (z-face states in shared memory, branch-free Roe path, compile-time
  * limiter; 2 CTAs per SM in FP32, 1 in FP64; tile path only); 3 = 320 threads
  * per group, one owned column or face-slab cell per thread, 2 CTAs per SM
- * (FP32-storage modes, tile and level paths); 4 = the default 160-thread
- * 3-CTA build with three input planes in flight instead of two
  * (FP32-storage modes, tile and level paths).  Where a variant does not
  * exist for a call (mode, path, HLLC or characteristic limiting) the default
  * shape runs.  Used by the autotuner; process-wide and unsynchronised like

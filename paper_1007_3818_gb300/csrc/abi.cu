@@ -93,7 +93,7 @@ extern "C" int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm) {
 }
 
 extern "C" int gamer_set_hydro_variant(int32_t variant) {
-    if (variant < 0 || variant > 4) return GAMER_E_PARAM;
+    if (variant < 0 || variant > 3) return GAMER_E_PARAM;
     gamer::hydro_variant() = variant;
     return GAMER_OK;
 }

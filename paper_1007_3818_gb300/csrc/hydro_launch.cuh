@@ -129,12 +129,6 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
         if constexpr (MODE == GAMER_MODE_F32 && SRC == 0) {
             if (var == 1 && want != 2) kern = hydro_step_kernel<MODE, 3, 1, SRC, 2>;
         }
-        // variant 4: the 3-CTA build with three input planes in flight
-        // (74.5 KB of shared memory per CTA: little L1 left for spills)
-        if (var == 4) {
-            kern = vl ? hydro_step_kernel<MODE, 3, 8, SRC, 3> : hydro_step_kernel<MODE, 3, 0, SRC, 3>;
-            smem = int(sizeof(Smem<T, 3>)) + int(PlaneLoader<SRC, 3, T>::kExtraSmem);
-        }
         // variant 3: 320 threads per group (one column per thread), 2 CTAs
         // per SM, three input planes in flight
         if (var == 3) {
