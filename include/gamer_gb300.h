@@ -495,8 +495,8 @@ int gamer_set_hydro_ctas_per_sm(int32_t mode, int32_t ctas_per_sm);
  * Riemann solver (FP32 3-CTA tile build only); 2 = two interleaved problems per
  * thread (z-face states in shared memory, branch-free Roe path, compile-time
  * limiter; 2 CTAs per SM in FP32, 1 in FP64; tile path only); 3 = 320 threads
- * per group, one owned column or face-slab cell per thread, 2 CTAs per SM
- * (FP32-storage modes, tile and level paths).  Where a variant does not
+ * per group, one owned column or face-slab cell per thread (2 CTAs per SM in
+ * the FP32-storage modes, 1 in FP64), tile and level paths.  Where a variant does not
  * exist for a call (mode, path, HLLC or characteristic limiting) the default
  * shape runs.  Used by the autotuner; process-wide and unsynchronised like
  * gamer_set_hydro_ctas_per_sm. */

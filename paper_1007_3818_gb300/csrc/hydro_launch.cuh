@@ -117,6 +117,14 @@ int hydro_launch(const typename Prec<MODE>::T* in, typename Prec<MODE>::T* out,
     if constexpr (MODE == GAMER_MODE_F64) {
         kern = vl ? hydro_step_kernel<MODE, 1, 8, SRC, 3> : hydro_step_kernel<MODE, 1, 0, SRC, 3>;
         smem = int(sizeof(Smem<T, 3>)) + extra;
+        // variant 3: 320 threads per group, still one CTA per SM (shared
+        // memory), twice the warps
+        if (var == 3) {
+            kern = vl ? hydro_step_kernel<MODE, 1, 8, SRC, 3, 320>
+                      : hydro_step_kernel<MODE, 1, 0, SRC, 3, 320>;
+            smem = int(sizeof(Smem<T, 3>)) + int(PlaneLoader<SRC, 3, T, 320>::kExtraSmem);
+            threads = 320;
+        }
     } else {
         if (want == 2) {
             kern = vl ? hydro_step_kernel<MODE, 2, 8, SRC, 3>

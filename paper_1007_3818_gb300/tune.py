@@ -4,8 +4,9 @@ What is chosen per GPU, precision mode and batch size:
 
   * threads per group: 160 (a thread owns two interior columns, or one and a
     face-slab cell; 320 predictions and 800 Riemann solves per plane divide
-    evenly) or 320 (variant 3: one column or slab cell per thread, 96
-    registers, 2 CTAs = 20 warps per SM);
+    evenly) or 320 (variant 3: one column or slab cell per thread; FP32
+    storage: 96 registers, 2 CTAs = 20 warps per SM; FP64: one CTA per SM,
+    10 warps instead of 5);
   * the register / shared-memory split of the 160-thread build: sized for 2
     CTAs per SM (no register spills, three input planes in flight) or for 3
     (more warps per SM, two planes in flight);
@@ -67,7 +68,7 @@ def tune_hydro(mode, inp, out, face_flux, dt, dh, status, partials, params, reps
     # every mode has the pair kernel, the FP32-storage modes the 320-thread
     # build
     if mode == native.GAMER_MODE_F64:
-        candidates = [(1, 0), (0, 2)]
+        candidates = [(1, 0), (0, 2), (0, 3)]
     elif mode == native.GAMER_MODE_F32:
         candidates = [(2, 0), (3, 0), (3, 1), (0, 2), (0, 3)]
     else:
@@ -134,9 +135,10 @@ def tune_hydro_level(mode, level, out, face_flux, gx, gy, gz, bc, dt, dh, status
         native.gamer_set_hydro_ctas_per_sm(mode, _cache[key]["ctas_per_sm"])
         native.gamer_set_hydro_variant(_cache[key]["variant"])
         return _cache[key]
-    # (CTAs per SM, variant): the 160-thread builds for 2 and 3 CTAs per SM,
-    # and the 320-thread build (FP32-storage modes)
-    candidates = [(1, 0)] if mode == native.GAMER_MODE_F64 else [(2, 0), (3, 0), (0, 3)]
+    # (CTAs per SM, variant): the 160-thread builds for 2 and 3 CTAs per SM
+    # (one in FP64) and the 320-thread build
+    candidates = ([(1, 0), (0, 3)] if mode == native.GAMER_MODE_F64
+                  else [(2, 0), (3, 0), (0, 3)])
     results = {}
     for c, v in candidates:
         native.gamer_set_hydro_ctas_per_sm(mode, c)

@@ -292,7 +292,8 @@ def test_sod_single_group_ten_steps(mode):
 VARIANTS = [pytest.param(F32, 0, id="f32-v0"), pytest.param(F32, 1, id="f32-v1"),
             pytest.param(F32, 2, id="f32-v2"), pytest.param(MIXED, 2, id="mixed-v2"),
             pytest.param(F64, 2, id="f64-v2"), pytest.param(F32, 3, id="f32-v3"),
-            pytest.param(MIXED, 3, id="mixed-v3"), pytest.param(FF, 3, id="ff-v3")]
+            pytest.param(MIXED, 3, id="mixed-v3"), pytest.param(FF, 3, id="ff-v3"),
+            pytest.param(F64, 3, id="f64-v3")]
 
 
 @pytest.fixture
@@ -513,7 +514,7 @@ def test_fused_level_launch_shapes(variant_guard, mode, ctas, bc, dims):
     _fused_vs_fill(mode, bc, dims)
 
 
-@pytest.mark.parametrize("mode", [F32, MIXED, FF], ids=["f32", "mixed", "ff"])
+@pytest.mark.parametrize("mode", [F32, MIXED, FF, F64], ids=["f32", "mixed", "ff", "f64"])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("dims", [(3, 2, 4), (1, 1, 1), (4, 1, 2)])
 def test_fused_level_320_threads_per_group(variant_guard, mode, bc, dims):
