@@ -70,7 +70,7 @@ KERNEL_SOURCES = ["paper_1007_3818_gb300/csrc/hydro_kernel.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_launch.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_f32.cu"]
 NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "bytes": 359712768 + 434654720,
-               "sources_sha256": "f9309340824f961b45b25fb9efd7007c22e2fe442771329618b1b1cd05531705"}
+               "sources_sha256": "7c924b2fff58aac0239a8980e56c15d763150abdd66b85a328dd90ea659d8051"}
 
 
 def kernel_sources_sha256():
