@@ -210,6 +210,57 @@ def test_hydro_dt_matches_oracle():
 
 
 # --------------------------------------------------------------------------
+def _partials_of_written_state(out, gamma):
+    """The per-group partials recomputed on the host, in FP64, from the state
+    the kernel wrote: max over cells of max_d |m_d / rho| + c, and the five
+    conserved sums (NumPy's pairwise FP64 summation, error ~1e-15 relative)."""
+    U = out.reshape(len(out), 5, -1)
+    r, E = U[:, 0], U[:, 4]
+    ke = 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2 + U[:, 3] ** 2) / r
+    c = np.sqrt(np.maximum(gamma * (gamma - 1) * (E - ke) / r, 0.0))
+    speed = (np.abs(U[:, 1:4]).max(axis=1) / r + c).max(axis=1)
+    return speed, U.sum(axis=2), np.abs(U).sum(axis=2)
+
+
+@pytest.mark.parametrize("mode", [F32, MIXED, FF, F64], ids=["f32", "mixed", "ff", "f64"])
+@pytest.mark.parametrize("path", ["tiles", "level"])
+def test_partials_are_the_sums_of_the_written_state(mode, path):
+    """The partials hold the conserved sums of the state the kernel wrote to
+    FP64 accuracy: in the FP32-storage modes each thread sums in compensated
+    float pairs (TwoSum), exact to about 2^-48 relative, so a plain FP32
+    accumulation (1e-7) or a dropped compensation term fails the 1e-12 bar.
+    The signal speed is the FP32 arithmetic's (approximate 1/rho and square
+    root): within 32 eps of the FP64 value."""
+    import torch
+    from paper_1007_3818_gb300 import native
+    g = 5 / 3
+    if path == "tiles":
+        tiles = wl.random_smooth_groups(7, seed=202, gamma=g)
+        out, _, st, part = gpu_advance(host_input(tiles, mode), 2e-3, 1 / 256, g, mode)
+    else:
+        gx = gy = gz = 2
+        U = wl.fourier_level(n=32, seed=303, gamma=g)
+        T = torch_dtype(mode)
+        G = gx * gy * gz
+        d_in = torch.from_numpy(np.ascontiguousarray(wl.level_to_groups(U))).to("cuda", T)
+        d_out = torch.empty_like(d_in)
+        dt = torch.full((G,), 1e-3, device="cuda", dtype=torch.float64)
+        dh = torch.full((G,), 1 / 64, device="cuda", dtype=torch.float64)
+        d_st = torch.full((G,), -1, device="cuda", dtype=torch.int32)
+        d_part = torch.full((G, 6), float("nan"), device="cuda", dtype=torch.float64)
+        native.hydro_advance_level(mode, d_in, d_out, None, gx, gy, gz, 0, dt, dh, d_st, d_part,
+                                   native.make_params(g))
+        torch.cuda.synchronize()
+        out, st, part = d_out.double().cpu().numpy(), d_st.cpu().numpy(), d_part.cpu().numpy()
+    assert np.all(st == 0), st
+    speed, sums, mag = _partials_of_written_state(out, g)
+    excess = np.abs(part[:, 1:] - sums) / (1e-12 * mag)
+    assert excess.max() <= 1.0, (excess.max(), np.unravel_index(excess.argmax(), excess.shape))
+    stol = 1e-13 if mode == F64 else 32 * 2.0 ** -23
+    assert np.all(np.abs(part[:, 0] - speed) <= stol * speed), np.abs(part[:, 0] / speed - 1).max()
+
+
+# --------------------------------------------------------------------------
 def _gpu_level_steps(U_level, gx, gy, gz, bc, dts, dh, gamma, mode):
     """Device-resident uniform-level steps: ghost fill -> advance, dt given."""
     import torch
