@@ -294,7 +294,8 @@ __device__ __forceinline__ void hlle_rot(const T L[5], const T R[5], const T FL[
 // Roe flux through a face whose normal is the first velocity component of the
 // rotated states L, R = (rho, m_n, m_t1, m_t2, E), with Harten's smoothing of
 // the acoustic eigenvalues and Harten-Hyman widths from the states beside each
-// acoustic wave.  Branch-free: returns true when the HLLE fallback must
+// acoustic wave.  Branch-free (in FP64 but for the entropy-fix smoothing,
+// see below): returns true when the HLLE fallback must
 // replace F (Roe sound speed squared not positive, or an intermediate state
 // with rho <= 0 or p <= 0; F is then meaningless).  Having no branch, the
 // whole solve is one block of instructions the scheduler can interleave.
@@ -344,10 +345,18 @@ __device__ __forceinline__ bool roe_main(const T L[5], const T R[5], const KCons
     const T d1 = max_(T(0), max_(K1u - (uL - cL), l1s - K1u));
     const T d5 = max_(T(0), max_(K5u - l5s, (uR + cR) - K5u));
     T e1 = abs_(K1u), e5 = abs_(K5u);
-    const T f1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
-    const T f5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
-    e1 = (e1 < d1) ? f1 : e1;
-    e5 = (e5 < d5) ? f5 : e5;
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the smoothing is rarely selected and its IEEE divisions are
+        // costly on the FP64 pipe, so it is evaluated only where selected
+        // (the same values)
+        if (e1 < d1) e1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
+        if (e5 < d5) e5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
+    } else {
+        const T f1 = (K1u * K1u + d1 * d1) * rcp_(T(2) * d1);
+        const T f5 = (K5u * K5u + d5 * d5) * rcp_(T(2) * d5);
+        e1 = (e1 < d1) ? f1 : e1;
+        e5 = (e5 < d5) ? f5 : e5;
+    }
     const T e2 = abs_(uT);
     const T s1 = e1 * a1, s2 = e2 * a2, s3 = e2 * a3, s4 = e2 * a4, s5 = e5 * a5;
     const T D0 = s1 + s2 + s5;
