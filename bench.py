@@ -70,7 +70,7 @@ KERNEL_SOURCES = ["paper_1007_3818_gb300/csrc/hydro_kernel.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_launch.cuh",
                   "paper_1007_3818_gb300/csrc/hydro_f32.cu"]
 NCU_TRAFFIC = {"mode": "f32", "groups": 4096, "bytes": 359066624 + 434415616,
-               "sources_sha256": "d5552c53fb7b526a4cce72347c5dff08b3bdd41db73ca381d5a01211cc07e65d"}
+               "sources_sha256": "7b2d4d21c85326624b8794479b9fd0056cd1c5aca2fe5e2a2cec2802cc3be3bf"}
 
 
 def kernel_sources_sha256():
