@@ -73,6 +73,29 @@ __device__ __forceinline__ float sq3_ff(float m1, float m2, float m3, float& se)
     return s;
 }
 
+// The same three on paired FP32 instructions (two independent lanes, each the
+// same IEEE operations in the same order as the scalar forms above).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2& e) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bp = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bp)))), __fadd2_rn(b, neg2(bp)));
+    return s;
+}
+__device__ __forceinline__ float2 two_prod2(float2 a, float2 b, float2& e) {
+    const float2 p = __fmul2_rn(a, b);
+    e = __ffma2_rn(a, b, neg2(p));
+    return p;
+}
+__device__ __forceinline__ float2 sq3_ff2(float2 m1, float2 m2, float2 m3, float2& se) {
+    float2 e1, e2, e3, t1, t2;
+    float2 s = two_prod2(m1, m1, e1);
+    s = two_sum2(s, two_prod2(m2, m2, e2), t1);
+    s = two_sum2(s, two_prod2(m3, m3, e3), t2);
+    se = __fadd2_rn(__fadd2_rn(__fadd2_rn(e1, e2), e3), __fadd2_rn(t1, t2));
+    return s;
+}
+
 template <class T, int RING = 2>
 struct alignas(16) Smem {
     T raw[RING][5 * kPlane + 4];  // ring of conserved input planes (TMA / cp.async)
@@ -405,6 +428,24 @@ __device__ __forceinline__ float2 pressure_x2(float2 r, float2 m, float2 ma, flo
         const float2 t = __ffma2_rn(pk(kc.gm1_lo, kc.gm1_lo), __fadd2_rn(E, pk(-ke.x, -ke.y)),
                                     pk(-gk.x, -gk.y));
         return __ffma2_rn(pk(kc.gm1, kc.gm1), E, t);
+    } else if constexpr (MODE == GAMER_MODE_FF) {
+        // the float-float recovery of pressure<FF>, both lanes at once
+        float2 se;
+        const float2 s = sq3_ff2(m, ma, mb, se);
+        const float2 il = __fmul2_rn(ir, __ffma2_rn(neg2(r), ir, pk(1.0f, 1.0f)));
+        float2 pe;
+        const float2 p = two_prod2(s, ir, pe);
+        const float2 half = pk(0.5f, 0.5f);
+        const float2 kh = __fmul2_rn(half, p);
+        const float2 kl = __fmul2_rn(half, __fadd2_rn(pe, __ffma2_rn(s, il, __fmul2_rn(se, ir))));
+        float2 de;
+        const float2 d = two_sum2(E, neg2(kh), de);
+        const float2 dl = __fadd2_rn(de, neg2(kl));
+        const float2 g = pk(kc.gm1, kc.gm1);
+        const float2 ph = __fmul2_rn(g, d);
+        const float2 pl = __fadd2_rn(__ffma2_rn(g, d, neg2(ph)),
+                                     __ffma2_rn(g, dl, __fmul2_rn(pk(kc.gm1_lo, kc.gm1_lo), d)));
+        return __fadd2_rn(ph, pl);
     } else {
         return pk(pressure<MODE>(r.x, m.x, ma.x, mb.x, E.x, ir.x, kc),
                   pressure<MODE>(r.y, m.y, ma.y, mb.y, E.y, ir.y, kc));
