@@ -198,6 +198,16 @@ __device__ __forceinline__ float p_mixed32(float E, float ke, float gm1, float g
     return fmaf(gm1, E, fmaf(gm1_lo, E - ke, -(gm1 * ke)));
 }
 
+// The mixed mode's FP32 recovery of one state; hi is set where the state
+// needs the FP64 recovery instead (ke > E / 2).
+template <class P>
+__device__ __forceinline__ float pressure_mixed32(float m1, float m2, float m3, float E, float ir,
+                                                  const KConst<float, P>& kc, bool& hi) {
+    const float ke = 0.5f * (m1 * m1 + m2 * m2 + m3 * m3) * ir;
+    hi = ke > kMixedKeFraction * E;
+    return p_mixed32(E, ke, kc.gm1, kc.gm1_lo);
+}
+
 // Pressure from a conserved state, given 1/rho in T.  MIXED: the selective
 // recovery above.
 template <int MODE, class T, class P>
@@ -422,8 +432,11 @@ __device__ __forceinline__ float2 pressure_x2(float2 r, float2 m, float2 ma, flo
         float2 s = __fmul2_rn(m, m);
         s = __ffma2_rn(ma, ma, s);
         s = __ffma2_rn(mb, mb, s);
-        const float2 ke = __fmul2_rn(__fmul2_rn(s, ir), pk(0.5f, 0.5f));
-        hi |= (ke.x > kMixedKeFraction * E.x) | (ke.y > kMixedKeFraction * E.y);
+        const float2 k2 = __fmul2_rn(s, ir);  // 2 ke
+        const float2 ke = __fmul2_rn(k2, pk(0.5f, 0.5f));
+        // ke > E / 2 as 2 ke > E (both sides scaled by 2 exactly)
+        static_assert(kMixedKeFraction == 0.5f, "the test below assumes 1/2");
+        hi |= (k2.x > E.x) | (k2.y > E.y);
         const float2 gk = __fmul2_rn(pk(kc.gm1, kc.gm1), ke);
         const float2 t = __ffma2_rn(pk(kc.gm1_lo, kc.gm1_lo), __fadd2_rn(E, pk(-ke.x, -ke.y)),
                                     pk(-gk.x, -gk.y));
@@ -959,6 +972,7 @@ template <int MODE, int NT = kThreads, class T, class P>
 __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __restrict__ W,
                                               uint32_t rbits, const KConst<T, P>& kc,
                                               uint32_t& st) {
+    uint32_t hi = 0;  // MIXED: bit r, cell r needs the FP64 recovery
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const int c = convert_cell<NT>(r);
@@ -971,11 +985,32 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
         W[1 * kPlane + c] = u[1] * ir;
         W[2 * kPlane + c] = u[2] * ir;
         W[3 * kPlane + c] = u[3] * ir;
-        W[4 * kPlane + c] = pressure<MODE>(u[0], u[1], u[2], u[3], u[4], ir, kc);
+        if constexpr (MODE == GAMER_MODE_MIXED) {
+            // FP32 recovery here; the cells that need FP64 are redone below,
+            // after the loop, in one rarely taken branch (a branch per cell
+            // would split the unrolled loop into separate blocks)
+            bool h = false;
+            W[4 * kPlane + c] = pressure_mixed32(u[1], u[2], u[3], u[4], ir, kc, h);
+            hi |= uint32_t(h) << r;
+        } else {
+            W[4 * kPlane + c] = pressure<MODE>(u[0], u[1], u[2], u[3], u[4], ir, kc);
+        }
         bool fin = true;
 #pragma unroll
         for (int q = 0; q < 5; ++q) fin &= finite_(u[q]);
         if (!fin & bool((rbits >> r) & 1u)) st |= GAMER_ST_BAD_INPUT;
+    }
+    if constexpr (MODE == GAMER_MODE_MIXED) {
+        if (hi) {
+            for (int r = 0; r < 3; ++r) {
+                if (!((hi >> r) & 1u)) continue;
+                const int c = convert_cell<NT>(r);
+                const T u0 = U[c], ir = rcp_(u0);
+                W[4 * kPlane + c] = pressure_fp64(u0, U[kPlane + c], U[2 * kPlane + c],
+                                                  U[3 * kPlane + c], U[4 * kPlane + c], ir,
+                                                  kc.gm1p);
+            }
+        }
     }
 }
 
