@@ -973,8 +973,42 @@ __device__ __forceinline__ void convert_plane(const T* __restrict__ U, T* __rest
                                               uint32_t rbits, const KConst<T, P>& kc,
                                               uint32_t& st) {
     uint32_t hi = 0;  // MIXED: bit r, cell r needs the FP64 recovery
+    // FF with 160 threads: cells 0 and 1 of the thread (both inside the
+    // plane) on the paired float-float recovery, each lane the same operations
+    // as the scalar one; cell 2 below
+    constexpr bool kPairFF = (MODE == GAMER_MODE_FF) && (NT == kThreads);
+    if constexpr (kPairFF) {
+        const int c0 = convert_cell<NT>(0), c1 = convert_cell<NT>(1);
+        T a[5], b[5];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 5; ++q) {
+            a[q] = U[q * kPlane + c0];
+            b[q] = U[q * kPlane + c1];
+        }
+        const T ia = rcp_(a[0]), ib = rcp_(b[0]);
+        W[0 * kPlane + c0] = a[0];
+        W[1 * kPlane + c0] = a[1] * ia;
+        W[2 * kPlane + c0] = a[2] * ia;
+        W[3 * kPlane + c0] = a[3] * ia;
+        W[0 * kPlane + c1] = b[0];
+        W[1 * kPlane + c1] = b[1] * ib;
+        W[2 * kPlane + c1] = b[2] * ib;
+        W[3 * kPlane + c1] = b[3] * ib;
+        bool unused = false;
+        const float2 p = pressure_x2<MODE>(pk(a[0], b[0]), pk(a[1], b[1]), pk(a[2], b[2]),
+                                           pk(a[3], b[3]), pk(a[4], b[4]), pk(ia, ib), kc, unused);
+        W[4 * kPlane + c0] = p.x;
+        W[4 * kPlane + c1] = p.y;
+        bool fa = true, fb = true;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            fa &= finite_(a[q]);
+            fb &= finite_(b[q]);
+        }
+        if ((!fa & bool(rbits & 1u)) | (!fb & bool((rbits >> 1) & 1u))) st |= GAMER_ST_BAD_INPUT;
+    }
+#pragma unroll
+    for (int r = kPairFF ? 2 : 0; r < 3; ++r) {
         const int c = convert_cell<NT>(r);
         if (c < 0) break;
         T u[5];
