@@ -1497,8 +1497,9 @@ __global__ void __launch_bounds__(NT, MINB)
                 const T cs = sqrt_(max_(c2, T(0)));
                 const T sp = max_(max_(abs_(o[1]), abs_(o[2])), abs_(o[3])) * abs_(ir) + cs;
                 smax = max_(smax, sp);
-                // paired sums in FP32 mode (1.5 % faster); the mixed and
-                // float-float builds measured 0.7 % slower with them
+                // paired sums in FP32 mode (1.5 % faster); the mixed build
+                // measured 0.7 % slower with them, so the other modes keep
+                // the scalar steps
                 if constexpr (MODE == GAMER_MODE_F32) {
                     sums.add5(o);
                 } else {
