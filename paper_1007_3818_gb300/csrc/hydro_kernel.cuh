@@ -843,15 +843,15 @@ __device__ __forceinline__ void faces_vanleer_x2(const float* __restrict__ lo, c
 }
 
 // Hancock half-step for the cell at plane index c (20x20 plane layout) of
-// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1.  Branch-free part:
-// fs[f] receives the evolved conserved face states x-, x+, y-, y+, z-, z+,
-// du the common half-step increment; returns whether all six are admissible
-// (rho > 0, p > 0).
-template <int MODE, int LIM, int REC = 0, class T, class P>
-__device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* __restrict__ W0,
-                                             const T* __restrict__ Wp, int c, T half_lam,
-                                             T igm1, const KConst<T, P>& kc, T fs[6][5],
-                                             T du[5]) {
+// plane k: Wm/W0/Wp are the primitive planes k-1, k, k+1.  fs[f] receives
+// the un-evolved conserved face states x-, x+, y-, y+, z-, z+ (the limited
+// reconstruction), du the common half-step increment.
+template <int LIM, int REC = 0, class T, class P>
+__device__ __forceinline__ void predict_unevolved(const T* __restrict__ Wm,
+                                                  const T* __restrict__ W0,
+                                                  const T* __restrict__ Wp, int c, T half_lam,
+                                                  T igm1, const KConst<T, P>& kc, T fs[6][5],
+                                                  T du[5]) {
     T wc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) wc[q] = W0[q * kPlane + c];
@@ -880,6 +880,17 @@ __device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* 
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) du[q] = half_lam * acc[q];
+}
+
+// The branch-free Hancock half-step: fs[f] receives the evolved face states
+// (the un-evolved ones + du); returns whether all six are admissible (rho > 0,
+// p > 0).
+template <int MODE, int LIM, int REC = 0, class T, class P>
+__device__ __forceinline__ bool predict_core(const T* __restrict__ Wm, const T* __restrict__ W0,
+                                             const T* __restrict__ Wp, int c, T half_lam,
+                                             T igm1, const KConst<T, P>& kc, T fs[6][5],
+                                             T du[5]) {
+    predict_unevolved<LIM, REC>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du);
     bool ok = true, und = false;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
@@ -911,15 +922,82 @@ __device__ __forceinline__ void predict_fallback(const T uc[5], const T du[5],
         for (int q = 0; q < 5; ++q) fs[f][q] = (kc.pfb == 0) ? uc[q] : fs[f][q] - du[q];
 }
 
+// The half-step of one cell with its outputs stored as they are produced: the
+// x-, x+, y-, y+ states into the face arrays at dxm, dxp, dym, dyp (component
+// 0; components kFaceStride apart), the z- and z+ states into zm, zp.  Each
+// state is stored as soon as it is evolved and tested, so that the six never
+// have to be held together in registers; the rare fallback (any state not
+// admissible: GAMER_ST_PREDICTOR_FALLBACK in st) then overwrites all six with
+// the cell average uc (option 0) or the un-evolved reconstruction, recovered
+// as (U + du) - du from the stored values (option 1).  The re-reads are
+// volatile, so that the compiler does not keep the stored values in registers
+// for them.  Same results as evolving all six, testing, then storing (which
+// the mixed build still does).
 template <int MODE, int LIM = -1, int REC = 0, class T, class P>
-__device__ __forceinline__ void predict(const T* __restrict__ Wm, const T* __restrict__ W0,
-                                        const T* __restrict__ Wp, const T uc[5], int c,
-                                        T half_lam, T igm1, const KConst<T, P>& kc,
-                                        T fs[6][5], uint32_t& st) {
-    T du[5];
-    if (!predict_core<MODE, LIM, REC>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du)) {
+__device__ __forceinline__ void predict_store(const T* __restrict__ Wm, const T* __restrict__ W0,
+                                              const T* __restrict__ Wp, const T uc[5], int c,
+                                              T half_lam, T igm1, const KConst<T, P>& kc,
+                                              T* dxm, T* dxp, T* dym, T* dyp, T zm[5], T zp[5],
+                                              uint32_t& st) {
+    T fs[6][5], du[5];
+    T* const dst[4] = {dxm, dxp, dym, dyp};
+    if constexpr (MODE == GAMER_MODE_MIXED) {
+        // the mixed build measured 0.7 % faster evolving all six first
+        if (!predict_core<MODE, LIM, REC>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du)) {
+            st |= GAMER_ST_PREDICTOR_FALLBACK;
+            predict_fallback(uc, du, kc, fs);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) dst[f][q * kFaceStride] = fs[f][q];
+            zm[q] = fs[4][q];
+            zp[q] = fs[5][q];
+        }
+        return;
+    }
+    predict_unevolved<LIM, REC>(Wm, W0, Wp, c, half_lam, igm1, kc, fs, du);
+    auto reread = [&](int f, int q) -> T {
+        return *reinterpret_cast<const volatile T*>(dst[f] + q * kFaceStride);
+    };
+    bool ok = true, und = false;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        T v[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] = fs[f][q] + du[q];
+        ok &= admissible<MODE>(v[0], v[1], v[2], v[3], v[4], und);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (f < 4) dst[f][q * kFaceStride] = v[q];
+            else if (f == 4) zm[q] = v[q];
+            else zp[q] = v[q];
+        }
+    }
+    if constexpr (MODE == GAMER_MODE_FF) {
+        if (und) {
+            States6 f6;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+#pragma unroll
+                for (int f = 0; f < 4; ++f) f6.v[f][q] = reread(f, q);
+                f6.v[4][q] = zm[q];
+                f6.v[5][q] = zp[q];
+            }
+            ok = admissible6_ff(f6);
+        }
+    }
+    if (!ok) {
         st |= GAMER_ST_PREDICTOR_FALLBACK;
-        predict_fallback(uc, du, kc, fs);
+        const bool avg = kc.pfb == 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                dst[f][q * kFaceStride] = avg ? uc[q] : reread(f, q) - du[q];
+            zm[q] = avg ? uc[q] : zm[q] - du[q];
+            zp[q] = avg ? uc[q] : zp[q] - du[q];
+        }
     }
 }
 
@@ -1540,44 +1618,19 @@ __global__ void __launch_bounds__(NT, MINB)
                 if (owner) {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc0[q] = Uk[q * kPlane + pc0];
-                    T fs[6][5];
-                    predict<MODE, kLim, kRec>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc, fs,
-                                                  st);
-                    if (inner) {
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) {
-                            S.xm[q * kFaceStride + fa0] = fs[0][q];
-                            S.xp[q * kFaceStride + fa0] = fs[1][q];
-                            S.ym[q * kFaceStride + fa0] = fs[2][q];
-                            S.yp[q * kFaceStride + fa0] = fs[3][q];
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        zm0[q] = fs[4][q];
-                        zpn0[q] = fs[5][q];
-                    }
+                    // (the x/y states of the planes outside the group, k = -1
+                    // and 16, are stored too: no solve reads them, and the
+                    // slots are free then)
+                    predict_store<MODE, kLim, kRec>(Wm, W0, Wp, uc0, pc0, half_lam, igm1, kc,
+                                                    S.xm + fa0, S.xp + fa0, S.ym + fa0,
+                                                    S.yp + fa0, zm0, zpn0, st);
                 }
                 if (kWide ? (!owner && inner) : (two || inner)) {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) uc1[q] = Uk[q * kPlane + pc_b];
-                    T fs[6][5];
-                    predict<MODE, kLim, kRec>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc, fs,
-                                                  st);
-                    if (inner) {
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) {
-                            S.xm[q * kFaceStride + o_xm] = fs[0][q];
-                            S.xp[q * kFaceStride + o_xp] = fs[1][q];
-                            S.ym[q * kFaceStride + o_ym] = fs[2][q];
-                            S.yp[q * kFaceStride + o_yp] = fs[3][q];
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        zm1[q] = fs[4][q];
-                        zpn1[q] = fs[5][q];
-                    }
+                    predict_store<MODE, kLim, kRec>(Wm, W0, Wp, uc1, pc_b, half_lam, igm1, kc,
+                                                    S.xm + o_xm, S.xp + o_xp, S.ym + o_ym,
+                                                    S.yp + o_yp, zm1, zpn1, st);
                 }
                 __syncthreads();
                 // plane k has been read: its slot takes plane k + RING
