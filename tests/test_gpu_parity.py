@@ -75,23 +75,30 @@ def test_fallback_paths_f64(pfb):
     assert (st[:3] & 1).all() and (st & 2).all()
 
 
-@pytest.mark.parametrize("mode", [F32, MIXED])
-def test_fallback_paths_fp32(mode):
-    """FP32 modes on the same stress tiles: the fallbacks fire and the state
-    stays close to the oracle (branch decisions may differ in a few cells, so
-    the bound is looser than the smooth-flow tolerance)."""
+@pytest.mark.parametrize("pfb", [0, 1])
+@pytest.mark.parametrize("mode", [F32, MIXED, FF], ids=["f32", "mixed", "ff"])
+def test_fallback_paths_fp32(mode, pfb):
+    """FP32-storage modes on the same stress tiles, both predictor-fallback
+    options: the fallbacks fire and the state stays close to the oracle
+    (branch decisions may differ in a few cells, so the bound is looser than
+    the smooth-flow tolerance).  The FP32 and float-float builds store each
+    predicted state as soon as it is tested and overwrite the stored states
+    when the fallback fires; this covers that path."""
     g = 1.4
     tiles = host_input(wl.stress_groups(3, seed=11, gamma=g), mode)
-    out, ff, st, _ = gpu_advance(tiles, 0.004, 1 / 16, g, mode)
-    r_out, _, r_st, _ = oracle.advance_groups(tiles, 0.004, 1 / 16, gamma=g)
+    out, ff, st, _ = gpu_advance(tiles, 0.004, 1 / 16, g, mode, predictor_fallback=pfb)
+    r_out, _, r_st, _ = oracle.advance_groups(tiles, 0.004, 1 / 16, gamma=g,
+                                              predictor_fallback=pfb)
     assert ((st & 3) == (r_st & 3)).all()
+    assert (r_st[:3] & 1).all()
     assert rel_l1_fields(out, r_out) <= 1e-3
     # the strong double rarefaction decides its fallbacks far from any
     # threshold, so there the FP32 modes meet the element-wise bound too
     # (HLLE faces and the states beside them included)
     tube = host_input(_tube_tile((1, -2, 0.4), (1, 2, 0.4), g), mode)
-    out, ff, st, _ = gpu_advance(tube, 0.004, 1 / 16, g, mode)
-    r_out, r_ff, r_st, _ = oracle.advance_groups(tube, 0.004, 1 / 16, gamma=g)
+    out, ff, st, _ = gpu_advance(tube, 0.004, 1 / 16, g, mode, predictor_fallback=pfb)
+    r_out, r_ff, r_st, _ = oracle.advance_groups(tube, 0.004, 1 / 16, gamma=g,
+                                                 predictor_fallback=pfb)
     assert np.array_equal(st, r_st) and (r_st & 2).all()
     assert_elementwise(out, r_out, mode, "state")
     assert_elementwise(ff, r_ff, mode, "face flux", state=False)
